@@ -1,0 +1,201 @@
+/*
+ * rips.h -- C ABI of the GB300 Vietoris–Rips persistence library (librips.so).
+ *
+ * Problem (Bauer, "Ripser: efficient computation of Vietoris–Rips persistence
+ * barcodes", arXiv 1908.02518): given a finite metric space as an n x n
+ * distance matrix, compute the persistence barcodes H_0 .. H_dim_max, with
+ * coefficients in the prime field Z/p, of the Vietoris–Rips filtration
+ * Rips_t(X) = { nonempty S : diam S <= t }  (Section 2, "Simplicial complexes and
+ * filtrations").  Bars are the intervals [f(sigma_i), f(sigma_j)) of the
+ * persistence pairs of the lexicographically refined filtration with
+ * f(sigma_i) < f(sigma_j), plus the essential intervals [f(sigma_i), inf)
+ * (Section 2, Proposition on simplexwise refinements).  Zero-length intervals
+ * are dropped.  f is the FP32 diameter, so every bar endpoint is a copy of an
+ * input entry (or 0 for H_0 births).
+ *
+ * Simplices are named by their index in the combinatorial number system
+ * (Section 2): the simplex on vertices a_0 < ... < a_d has index
+ * sum_l C(a_l, l+1).
+ *
+ * Common conventions for every entry point:
+ *  - dist: n x n row-major FP32; only the strict lower triangle dist[i*n + j]
+ *    with i > j is read; the diagonal and the upper triangle are ignored.
+ *    Entries must be finite and >= 0 (NaN, inf or negative -> RIPS_ERR_BAD_ARG).
+ *  - threshold: simplices with diameter <= threshold are included (Section 2).
+ *    +inf or NaN means "no threshold": the enclosing radius
+ *    min_x max_{y != x} d(x, y) is used, beyond which the complex is a cone and
+ *    the barcode cannot change (Section 4, "Input").  A negative threshold is
+ *    RIPS_ERR_BAD_ARG.
+ *  - p: prime, 2 <= p < 65536 (Section 4, "Coefficients"); otherwise
+ *    RIPS_ERR_BAD_MODULUS.
+ *  - dim_max >= 0 and n >= 1, else RIPS_ERR_BAD_ARG.  n is at most 46340 (the
+ *    n x n rank matrix and the neighbour lists use 32-bit offsets); dim_max is at
+ *    most 7.  C(n, dim_max + 2) must be below 2^63 and
+ *    every filtration key (diameter rank bits + simplex index bits) must fit in
+ *    64 bits, else RIPS_ERR_OVERFLOW (the paper uses 64-bit indices, Section 4).
+ *  - Every function returns RIPS_OK (0) on success or a negative status and
+ *    never throws.  Calls on the same device are serialised internally; work is
+ *    issued on the given CUDA stream (NULL = legacy default stream).
+ *  - All computation runs on the current CUDA device.  Result objects are owned
+ *    by the library until rips_result_free.
+ */
+#ifndef RIPS_H
+#define RIPS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RIPS_API __attribute__((visibility("default")))
+
+enum rips_status {
+  RIPS_OK = 0,
+  RIPS_ERR_BAD_ARG = -1,        /* invalid size, pointer, distance or threshold */
+  RIPS_ERR_BAD_MODULUS = -2,    /* p not a prime in [2, 65536) */
+  RIPS_ERR_OVERFLOW = -3,       /* simplex index or filtration key exceeds 64 bits */
+  RIPS_ERR_OOM = -4,            /* device or host allocation failed */
+  RIPS_ERR_CUDA = -5,           /* a CUDA runtime call failed */
+  RIPS_ERR_DEVICE_TIMEOUT = -6, /* a bounded device loop hit its iteration limit */
+  RIPS_ERR_INTERNAL = -7        /* an internal consistency check failed */
+};
+
+/* One bar of the barcode.  death = +inf for an essential class. */
+typedef struct rips_bar {
+  int32_t dim;            /* homology dimension of the bar */
+  float birth;            /* diameter of the birth simplex (0 in H_0) */
+  float death;            /* diameter of the death simplex, +inf if essential */
+  int32_t cloud;          /* cloud number in a batched call, 0 otherwise */
+  uint64_t birth_simplex; /* index of the birth simplex (a dim-simplex) */
+  uint64_t death_simplex; /* index of the death simplex (a (dim+1)-simplex), UINT64_MAX if essential */
+} rips_bar_t;
+
+/* Per-dimension counters, the categories of Table 2 of the paper. */
+typedef struct rips_stats {
+  int64_t simplices;        /* d-simplices with diameter <= threshold */
+  int64_t apparent_cofacet; /* of which in a zero apparent pair (sigma, tau) as sigma */
+  int64_t apparent_facet;   /* of which in a zero apparent pair (rho, sigma) as sigma */
+  int64_t cleared;          /* of which pivots of the (d-1)-reduction found in its table */
+  int64_t columns;          /* columns reduced: the rest */
+  int64_t emergent;         /* columns whose first pivot was never contested */
+  int64_t pairs;            /* persistence pairs (d, d+1) found by the reduction */
+  int64_t zero_pairs;       /* of which zero persistence */
+  int64_t essential;        /* essential classes in dimension d */
+  int64_t reduction_steps;  /* column additions performed */
+  int64_t rounds;           /* claim/reduce rounds of the reduction */
+} rips_stats_t;
+
+typedef struct rips_result rips_result_t;
+
+/*
+ * rips_barcodes -- barcode of one distance matrix held in HOST memory.
+ * The matrix is copied to the device on `stream`; the bars are copied back.
+ * out: receives a new result object (NULL on failure).
+ */
+RIPS_API int rips_barcodes(const float* dist, int64_t n, int32_t dim_max, float threshold,
+                           uint32_t p, rips_result_t** out);
+
+/* Same, for a distance matrix already in DEVICE memory (not modified), with the
+ * work issued on `cuda_stream` (a cudaStream_t, or NULL). */
+RIPS_API int rips_barcodes_device(const float* d_dist, int64_t n, int32_t dim_max, float threshold,
+                                  uint32_t p, void* cuda_stream, rips_result_t** out);
+
+/*
+ * rips_distance_matrix_device -- Euclidean distances of n points with k FP32
+ * coordinates each (row-major, DEVICE memory) into d_dist (n x n, DEVICE,
+ * written in full).  Each entry is computed in float64 from the FP32
+ * coordinates (squared differences summed in coordinate order, each operation
+ * separately rounded, then a correctly rounded square root) and rounded to FP32.
+ */
+RIPS_API int rips_distance_matrix_device(const float* d_points, int64_t n, int32_t k, float* d_dist,
+                                         void* cuda_stream);
+
+/*
+ * rips_barcodes_batched -- barcodes of `batch` independent point clouds in one
+ * pass.  d_points: all clouds' FP32 coordinates concatenated (DEVICE, row-major,
+ * k per point); d_offsets: batch+1 point offsets (HOST).  The distances of every
+ * cloud are computed on the device by the rule of rips_distance_matrix_device.
+ * The bars of cloud c carry cloud = c.
+ */
+RIPS_API int rips_barcodes_batched(const float* d_points, const int64_t* offsets, int32_t batch,
+                                   int32_t k, int32_t dim_max, float threshold, uint32_t p,
+                                   void* cuda_stream, rips_result_t** out);
+
+/*
+ * rips_barcodes_backward -- gradient of a loss L(bars) with respect to the
+ * point coordinates of the clouds of a result computed by
+ * rips_barcodes_batched (or by rips_barcodes_device on distances produced by
+ * rips_distance_matrix_device, with batch = 1).  d_points and k are the
+ * coordinates the distances were computed from (DEVICE, as for the forward).
+ * grad_birth, grad_death: dL/dbirth and dL/ddeath per bar, in the order of
+ * rips_result_bars over all clouds (DEVICE, FP32; essential deaths ignored).
+ * Each finite bar endpoint is the length of one critical edge, the longest
+ * edge of its simplex (ties: the edge with the smallest index).  The gradient
+ * is scattered into d_grad_points (same layout as d_points, DEVICE, FP32,
+ * accumulated: the caller zeroes it) through d|x_a - x_b| / dx_a.
+ * If d_grad_dist is not NULL it receives dL/d dist[i][j] (i > j) for each cloud's
+ * n x n block laid out back to back (DEVICE, FP32, accumulated).
+ */
+RIPS_API int rips_barcodes_backward(const rips_result_t* res, const float* d_points, int32_t k,
+                                    const float* grad_birth, const float* grad_death,
+                                    float* d_grad_points, float* d_grad_dist, void* cuda_stream);
+
+/* Number of bars of cloud `cloud` in dimension `dim` (dim = -1: all dims);
+ * cloud = -1: all clouds.  Negative status on a bad argument. */
+RIPS_API int64_t rips_result_num_bars(const rips_result_t* res, int32_t cloud, int32_t dim);
+
+/* Host pointer to those bars (owned by the result), ordered by cloud, then
+ * dimension, then birth, death and birth simplex index; NULL if none. */
+RIPS_API const rips_bar_t* rips_result_bars(const rips_result_t* res, int32_t cloud, int32_t dim);
+
+/* Number of clouds, dim_max and the effective threshold of cloud `cloud`. */
+RIPS_API int32_t rips_result_num_clouds(const rips_result_t* res);
+RIPS_API int32_t rips_result_dim_max(const rips_result_t* res);
+RIPS_API float rips_result_threshold(const rips_result_t* res, int32_t cloud);
+
+/* Statistics of cloud `cloud` in dimension `dim`. */
+RIPS_API int rips_result_stats(const rips_result_t* res, int32_t cloud, int32_t dim,
+                               rips_stats_t* out);
+
+/* Device-side timing of the last call's phases in milliseconds (CUDA events on
+ * the call's stream), for profiling: index 0 = prologue + H_0, then one entry
+ * per dimension 1..dim_max.  Returns the number of entries written. */
+RIPS_API int32_t rips_result_phase_ms(const rips_result_t* res, float* out, int32_t cap);
+
+/* Kernel classes for rips_result_kernel_ms. */
+enum rips_kernel_class {
+  RIPS_K_PROLOGUE = 0,  /* validation, radius, edge keys, ranks, rank matrix, neighbours */
+  RIPS_K_EDGE_SORT = 1, /* radix sort of the edges into filtration order */
+  RIPS_K_H0 = 2,        /* spanning forest and elder rule */
+  RIPS_K_ENUMERATE = 3, /* d-simplex enumeration */
+  RIPS_K_APPARENT = 4,  /* zero-apparent-pair / clearing test and compaction */
+  RIPS_K_COL_SORT = 5,  /* radix sort of the columns into processing order */
+  RIPS_K_PIVOT_INIT = 6,/* first pivots (emergent shortcut) */
+  RIPS_K_REDUCE = 7,    /* claim and reduce rounds */
+  RIPS_K_READOUT = 8,   /* bars and statistics */
+  RIPS_KERNEL_CLASSES = 9
+};
+
+/* Profiling aid (no counterpart in the paper): when enabled, every later call
+ * records CUDA events on its stream around the launches of each kernel class.
+ * Returns the previous setting. */
+RIPS_API int rips_set_kernel_timing(int enable);
+
+/* Total device time (ms) and number of timed regions of kernel class `cls` in
+ * the call that produced `res` (zero when timing was off). */
+RIPS_API int rips_result_kernel_ms(const rips_result_t* res, int32_t cls, float* ms, int64_t* regions);
+
+RIPS_API void rips_result_free(rips_result_t* res);
+
+/* Human-readable name of a status code (static string). */
+RIPS_API const char* rips_status_string(int status);
+
+/* Number of kernel launches issued by this library on the calling thread
+ * since the last reset (a profiling aid). */
+RIPS_API int64_t rips_kernel_launch_count(int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RIPS_H */

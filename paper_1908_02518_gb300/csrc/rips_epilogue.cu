@@ -1,0 +1,65 @@
+// Canonical order of the output bars: by cloud and dimension, then birth, then
+// death, then birth simplex index -- three stable LSD radix sorts of a
+// permutation (least significant key first), then one gather.
+#include "rips_internal.cuh"
+
+namespace rips {
+
+namespace {
+
+__global__ void iota_kernel(uint32_t* __restrict__ p, uint32_t n) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = i;
+}
+
+// key of bar perm[i] for pass `which`
+__global__ void bar_key_kernel(const rips_bar_t* __restrict__ bars, const uint32_t* __restrict__ perm, uint32_t n,
+                               int which, uint64_t* __restrict__ keys) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const rips_bar_t b = bars[perm[i]];
+  uint64_t k;
+  if (which == 0) k = b.birth_simplex;
+  else if (which == 1) k = ((uint64_t)__float_as_uint(b.birth) << 32) | __float_as_uint(b.death);
+  else k = ((uint64_t)(uint32_t)b.cloud << 8) | (uint32_t)b.dim;
+  keys[i] = k;
+}
+
+__global__ void gather_bars_kernel(const rips_bar_t* __restrict__ in, const uint32_t* __restrict__ perm, uint32_t n,
+                                   rips_bar_t* __restrict__ out) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = in[perm[i]];
+}
+
+}  // namespace
+
+size_t bar_order_temp_bytes(uint32_t nb) { return sort_temp_bytes(nb); }
+
+cudaError_t launch_bar_order(rips_bar_t* bars, rips_bar_t* bars_alt, uint32_t nb, uint64_t* k0, uint64_t* k1,
+                             uint32_t* p0, uint32_t* p1, void* tmp, size_t tmp_bytes, int simplex_bits,
+                             int group_bits, cudaStream_t s) {
+  if (nb == 0) return cudaSuccess;
+  const int blocks = (int)((nb + 255) / 256);
+  iota_kernel<<<blocks, 256, 0, s>>>(p0, nb);
+  note_launch();
+  uint32_t* perm = p0;
+  uint32_t* perm_alt = p1;
+  const int bits[3] = {simplex_bits, 64, 8 + group_bits};
+  for (int which = 0; which < 3; ++which) {
+    bar_key_kernel<<<blocks, 256, 0, s>>>(bars, perm, nb, which, k0);
+    note_launch();
+    bool alt = false;
+    cudaError_t e = radix_sort_u64(k0, k1, perm, perm_alt, nb, bits[which], tmp, tmp_bytes, &alt, s);
+    if (e != cudaSuccess) return e;
+    if (alt) {
+      uint32_t* t = perm;
+      perm = perm_alt;
+      perm_alt = t;
+    }
+  }
+  gather_bars_kernel<<<blocks, 256, 0, s>>>(bars, perm, nb, bars_alt);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace rips

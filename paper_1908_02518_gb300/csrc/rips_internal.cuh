@@ -1,0 +1,213 @@
+// Internal declarations shared by the CUDA translation units of librips.
+//
+// Layout conventions used throughout:
+//  * R (rank matrix): n x n uint32, full and symmetric.  R[i*n+j] is the rank of
+//    the edge length d(i,j) among the distinct edge lengths <= threshold, in
+//    increasing order, or RANK_INF if d(i,j) > threshold or i == j.  Every
+//    simplex diameter is an edge length, so comparing ranks compares diameters
+//    exactly (Section 2: the Rips filtration is the sublevel filtration of the
+//    diameter), and all later kernels work on integers only.
+//  * Binomial table: uint64, k-major: binom[k*(n+1) + i] = C(i, k) for
+//    0 <= k <= kmax, 0 <= i <= n (saturating at UINT64_MAX).
+//  * A d-simplex is identified by its index in the combinatorial number system
+//    (Section 2) and carries the rank of its diameter.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/rips.h"
+
+namespace rips {
+
+constexpr uint32_t RANK_INF = 0xFFFFFFFFu;
+constexpr uint64_t IDX_NONE = ~0ull;
+constexpr int MAX_DIM = 8;  // largest simplex dimension handled (vertices per simplex <= 9)
+
+// device error flag bits (written with atomicOr into Workspace::d_err)
+enum : uint32_t {
+  ERRF_TIMEOUT = 1u,       // a bounded loop hit its limit
+  ERRF_TABLE_FULL = 2u,    // pivot hash table probe limit reached
+  ERRF_INTERNAL = 4u,      // consistency check failed
+  ERRF_ARENA = 8u,         // V arena exhausted (retry after growth)
+  ERRF_BAD_INPUT = 16u,    // NaN / negative / infinite distance
+  ERRF_OUT_OVERFLOW = 32u  // an output list exceeded its capacity (retry after growth)
+};
+
+// ------------------------------------------------------------------ kernel launch accounting
+void note_launch();
+
+// ------------------------------------------------------------------ device helpers
+__device__ __forceinline__ uint64_t binom(const uint64_t* __restrict__ tab, int stride, int i, int k) {
+  return tab[(size_t)k * stride + i];
+}
+
+// Largest v in [lo, hi] with C(v, k) <= N (the Lemma of Section 4,
+// "Vertices and simplices"), by binary search.  Requires C(lo, k) <= N.
+__device__ __forceinline__ int max_vertex(const uint64_t* __restrict__ tab, int stride, int lo, int hi,
+                                          int k, uint64_t N) {
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (binom(tab, stride, mid, k) <= N) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Vertices of the d-simplex with index N, written in decreasing order
+// v[0] > v[1] > ... > v[d].
+__device__ __forceinline__ void decode_simplex(const uint64_t* __restrict__ tab, int stride, int n,
+                                               uint64_t N, int d, int* v) {
+  int hi = n - 1;
+  for (int k = d + 1; k >= 1; --k) {
+    int x = max_vertex(tab, stride, k - 1, hi, k, N);
+    v[d + 1 - k] = x;
+    N -= binom(tab, stride, x, k);
+    hi = x - 1;
+  }
+}
+
+// Z/p helpers (p < 2^16 so products fit in 32 bits)
+__device__ __forceinline__ uint32_t mod_inv(uint32_t a, uint32_t p) {
+  // extended Euclid on (a, p), p prime, a != 0
+  int32_t t = 0, nt = 1;
+  int32_t r = (int32_t)p, nr = (int32_t)(a % p);
+  while (nr != 0) {
+    int32_t q = r / nr;
+    int32_t tmp = t - q * nt;
+    t = nt;
+    nt = tmp;
+    tmp = r - q * nr;
+    r = nr;
+    nr = tmp;
+  }
+  if (t < 0) t += (int32_t)p;
+  return (uint32_t)t;
+}
+
+__device__ __forceinline__ void set_error(uint32_t* err, uint32_t bit) { atomicOr(err, bit); }
+
+__host__ __device__ __forceinline__ int bit_width64(uint64_t x) {
+  int b = 0;
+  while (x) {
+    ++b;
+    x >>= 1;
+  }
+  return b;
+}
+
+// ------------------------------------------------------------------ host-side launchers
+// (defined in the .cu files; every launcher returns a cudaError_t of the launch)
+
+// rips_prologue.cu
+cudaError_t launch_binomial_table(uint64_t* tab, int n, int kmax, cudaStream_t s);
+cudaError_t launch_validate_rowmax(const float* D, int n, uint32_t* rowmax_bits, uint32_t* err,
+                                   cudaStream_t s);
+cudaError_t launch_threshold(const uint32_t* rowmax_bits, int n, float threshold, float* t_eff,
+                             cudaStream_t s);
+cudaError_t launch_edge_keys(const float* D, int n, const float* t_eff, uint64_t* keys, uint32_t* count,
+                             uint32_t cap, cudaStream_t s);
+cudaError_t launch_assign_ranks(const uint64_t* sorted_keys, uint32_t num_edges, uint32_t* flags,
+                                uint32_t* scan_tmp, size_t scan_tmp_bytes, uint32_t* edge_rank,
+                                float* rank_value, uint32_t* num_ranks, cudaStream_t s);
+cudaError_t launch_fill_rank_matrix(const uint64_t* sorted_keys, const uint32_t* edge_rank,
+                                    uint32_t num_edges, int n, uint32_t* R, cudaStream_t s);
+cudaError_t launch_neighbor_counts(const uint32_t* R, int n, uint32_t* deg, cudaStream_t s);
+cudaError_t launch_neighbor_fill(const uint32_t* R, int n, const uint32_t* off, uint32_t* nbr,
+                                 cudaStream_t s);
+cudaError_t launch_distance_matrix(const float* pts, int n, int k, float* D, cudaStream_t s);
+
+// rips_scan.cu: exclusive scan of uint32 (in place allowed); returns total in *d_total if non-null
+size_t scan_temp_bytes(uint32_t n);
+cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, uint32_t n, void* tmp,
+                                  uint32_t* d_total, cudaStream_t s);
+
+// rips_sort.cu: LSD radix sort of 64-bit keys (optionally with uint32 values),
+// over bits [0, key_bits).  Result in *out (may alias one of the two buffers).
+size_t sort_temp_bytes(uint32_t n);
+cudaError_t radix_sort_u64(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t* vals_alt,
+                           uint32_t n, int key_bits, void* tmp, size_t tmp_bytes, bool* result_in_alt,
+                           cudaStream_t s);
+
+// One dimension of the reduction (rips_dim.cu)
+struct DimArgs {
+  int n, d;                        // columns are d-simplices
+  const uint32_t* R;               // rank matrix
+  const uint32_t* nbr_off;         // neighbour lists, decreasing order
+  const uint32_t* nbr;
+  const uint64_t* binom;           // global binomial table, stride n+1
+  int kmax;                        // rows 0..kmax of the table are staged
+  int smem_binom;                  // stage the table in shared memory
+  uint32_t p;
+  int row_bits;                    // bits of a (d+1)-simplex index
+  int col_bits;                    // bits of a d-simplex index
+  uint32_t rank_max;               // largest diameter rank
+  uint32_t* err;
+};
+
+
+// Reduction state (device pointers) shared by the reduction kernels
+struct RedState {
+  // columns in processing order
+  const uint64_t* col_keys;   // ((rank_max - rank) << col_bits) | idx
+  uint32_t ncols;
+  // per-column state
+  uint64_t* piv_key;          // row key of the pivot, IDX_NONE for a zero column
+  uint32_t* piv_coef;
+  uint32_t* v_off;            // V_j in the arena (v_len == 0: V_j = e_j)
+  uint32_t* v_len;
+  uint8_t* reduced;           // 1 once the column has been added to
+  // V arena
+  uint64_t* v_idx;
+  uint32_t* v_rank;
+  uint32_t* v_coef;
+  unsigned long long* v_top;
+  unsigned long long v_cap;
+  // pivot table
+  uint64_t* t_keys;
+  uint32_t* t_vals;
+  uint64_t t_mask;
+  // work lists
+  uint32_t* claim_list;
+  uint32_t* claim_count;
+  uint32_t* reduce_list;
+  uint32_t* reduce_count;
+  unsigned long long* steps;
+  uint32_t* err;
+};
+
+
+// from rips_h0.cu
+cudaError_t run_h0(int n, const uint64_t* sorted_keys, uint32_t m, uint32_t* eu, uint32_t* ev, uint32_t* comp,
+                   uint32_t* best, uint32_t* parent, uint8_t* in_forest, uint32_t* flags, uint32_t* fpos,
+                   void* scan_tmp, uint32_t* d_nf, uint32_t* gtop, rips_bar_t* bars, uint32_t* nbars,
+                   uint32_t bar_cap, int cloud, unsigned long long* stats, uint32_t* err, cudaStream_t s);
+
+// from rips_dim.cu
+cudaError_t launch_enumerate(const DimArgs& a, const uint64_t* pidx, const uint32_t* prank, uint32_t np,
+                             uint64_t* out_idx, uint32_t* out_rank, unsigned long long* count,
+                             unsigned long long cap, cudaStream_t st);
+cudaError_t launch_edges_to_simplices(const uint64_t* keys, const uint32_t* erank, uint32_t m, uint64_t* sidx,
+                                      uint32_t* srank, cudaStream_t st);
+cudaError_t launch_test(const DimArgs& a, const uint64_t* sidx, const uint32_t* srank, uint32_t ns,
+                        const uint8_t* cleared_flag, const uint64_t* prev_keys, uint64_t prev_mask,
+                        uint64_t* col_keys, uint32_t* ncols, uint32_t col_cap, unsigned long long* stats,
+                        cudaStream_t st);
+cudaError_t launch_init(const DimArgs& a, const RedState& s, cudaStream_t st);
+cudaError_t launch_claim(const DimArgs& a, const RedState& s, uint32_t count, cudaStream_t st);
+cudaError_t launch_reduce(const DimArgs& a, const RedState& s, uint32_t count, cudaStream_t st);
+cudaError_t launch_readout(const DimArgs& a, const RedState& s, const float* rank_value, int cloud,
+                           rips_bar_t* bars, uint32_t* nbars, uint32_t bar_cap, unsigned long long* stats,
+                           cudaStream_t st);
+
+// from rips_epilogue.cu
+cudaError_t launch_bar_order(rips_bar_t* bars, rips_bar_t* bars_alt, uint32_t nb, uint64_t* k0, uint64_t* k1,
+                             uint32_t* p0, uint32_t* p1, void* tmp, size_t tmp_bytes, int simplex_bits,
+                             int group_bits, cudaStream_t s);
+size_t bar_order_temp_bytes(uint32_t nb);
+
+// from rips_backward.cu
+cudaError_t launch_backward(const rips_bar_t* bars, uint32_t nb, const float* pts, int k, const int64_t* pt_off,
+                            const int64_t* dist_off, const float* gbirth, const float* gdeath, float* gx, float* gd,
+                            cudaStream_t s);
+
+}  // namespace rips
