@@ -39,6 +39,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--profile", action="store_true",
+                    help="warm-up calls then exactly one barcode call, for ncu launch lists and captures")
     return ap.parse_args()
 
 
@@ -178,6 +180,15 @@ def main():
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
+
+    if args.profile:
+        for _ in range(args.warmup):
+            rg.barcodes(dev_d, w.dim_max, w.threshold, w.p)
+        torch.cuda.synchronize()
+        res = rg.barcodes(dev_d, w.dim_max, w.threshold, w.p)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": w.name, "bars": len(res.bars), "phase_ms": res.phase_ms}))
+        return 0
 
     # warm-up (also sizes the workspace)
     for _ in range(max(3, args.warmup)):

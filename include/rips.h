@@ -84,6 +84,8 @@ typedef struct rips_stats {
   int64_t essential;        /* essential classes in dimension d */
   int64_t reduction_steps;  /* column additions performed */
   int64_t rounds;           /* claim/reduce rounds of the reduction */
+  int64_t longest_chain;    /* most additions made by one column in one round */
+  int64_t compacted_entries;/* working-column entries merged by run compactions */
 } rips_stats_t;
 
 typedef struct rips_result rips_result_t;

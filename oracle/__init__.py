@@ -47,7 +47,8 @@ class _Bar(C.Structure):
 
 class _Stats(C.Structure):
     _fields_ = [("simplices", C.c_int64), ("columns", C.c_int64), ("pairs", C.c_int64),
-                ("zero_pairs", C.c_int64), ("essential", C.c_int64), ("apparent_zero", C.c_int64)]
+                ("zero_pairs", C.c_int64), ("essential", C.c_int64), ("apparent_zero", C.c_int64),
+                ("additions", C.c_int64)]
 
 
 def _load():

@@ -465,6 +465,7 @@ static int oracle_def(const float* D, int64_t n, int32_t dim_max, float t, uint3
       int64_t k = owner[piv];
       if (k < 0) break;
       uint32_t lam = (uint32_t)(((uint64_t)R[j][Rl[j] - 1].c * modinv(R[k][Rl[k] - 1].c, p)) % p);
+      res->stats[AT(filt, fsimp, j).dim < 63 ? AT(filt, fsimp, j).dim : 63].additions++;
       rc = col_axpy(&R[j], &Rl[j], &cap, R[k], Rl[k], lam, p);
       if (rc) break;
     }
@@ -988,6 +989,7 @@ static int oracle_coh(const float* D, int64_t n, int32_t dim_max, float t, uint3
           if (k < 0) break;
           uint32_t lam = (uint32_t)(((uint64_t)pv.c * modinv(pivc[k], p)) % p);
           uint32_t neg = (p - lam) % p;
+          res->stats[d].additions++;
           /* R_j <- R_j - lam * D V_k, recomputing D V_k (implicit reduction) */
           tmp.n = 0;
           simp sk = AT(cols, simp, k);

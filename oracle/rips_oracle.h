@@ -48,6 +48,7 @@ typedef struct {
   int64_t zero_pairs;      /* of which persistence is zero */
   int64_t essential;       /* essential classes in dim d */
   int64_t apparent_zero;   /* ORACLE_DEF only: zero-persistence apparent pairs (d, d+1) */
+  int64_t additions;       /* column additions made by the reduction */
 } oracle_dim_stats;
 
 typedef struct oracle_result oracle_result;

@@ -93,12 +93,12 @@ struct Workspace {
   Buf eu, ev, comp, best, parent, gtop, inforest, fpos, nf;
   Buf sidx[2], srank[2], scount;
   Buf ckeys, ckeys_alt, ccount, sorttmp;
-  Buf piv_key, piv_coef, v_off, v_len, reduced, claim, reduce, lists;
-  Buf v_idx, v_rank, v_coef, v_top;
+  Buf piv_key, piv_coef, r_off, r_len, reduced, claim, reduce, lists;
+  Buf r_key, r_coef, r_top;
   Buf tkeys[2], tvals[2];
   Buf bars, bars_alt, bk0, bk1, bp0, bp1, bartmp, nbars;
-  Buf stats, bwd_bars, bwd_off, cdist;
-  size_t v_cap = 0;
+  Buf stats, bwd_bars, bwd_off, cdist, clouds, tileoff, vcloud, ccounts;
+  size_t r_cap = 0;
   HostPinned* pinned = nullptr;
   cudaEvent_t tev[16] = {};
   bool events = false;
@@ -240,148 +240,223 @@ uint32_t pow2_at_least(uint64_t x) {
 }
 
 // One cloud on the device: appends its bars (device) at *nbars and writes stats.
-struct CloudOut {
+// Everything one call produces besides the bars (which stay on the device).
+struct BatchOut {
+  std::vector<float> t_eff;                 // per cloud
+  std::vector<rips_stats_t> stats;          // clouds * (dim_max + 1)
+  std::vector<float> phase_ms;
   float kernel_ms[RIPS_KERNEL_CLASSES] = {};
   int64_t kernel_regions[RIPS_KERNEL_CLASSES] = {};
-  float t_eff = 0;
-  std::vector<rips_stats_t> stats;
-  std::vector<float> phase_ms;
+  uint32_t nbars = 0;
 };
 
 int sync_read(Workspace& w, cudaStream_t s) {
+  (void)w;
   CK(cudaStreamSynchronize(s));
   return RIPS_OK;
 }
 
-int run_cloud(Workspace& w, const float* dD, int n, int dim_max, float threshold, uint32_t p, int cloud,
-              cudaStream_t s, uint32_t* h_nbars_io, CloudOut& out) {
+int bits_of_count(uint64_t count) { return std::max(1, bit_width64(count ? count - 1 : 0)); }
+
+// The whole barcode pipeline for a batch of clouds whose n_c x n_c distance
+// matrices lie back to back at dD.  Bars are left in w.bars (device), with the
+// statistics, thresholds and timings in `out`.
+int run_batch(Workspace& w, const float* dD, const std::vector<int64_t>& ns, int dim_max, float threshold,
+              uint32_t p, cudaStream_t s, BatchOut& out) {
   HostPinned* hp = w.pinned;
+  const int C = (int)ns.size();
   const int kmax = dim_max + 2;
+  const int SPC = (dim_max + 1) * 16;  // statistics counters per cloud
   w.kev_used = 0;
-  out.stats.assign(dim_max + 1, rips_stats_t{});
   if (w.events) CK(cudaEventRecord(w.tev[0], s));
 
+  // ---------------- cloud table
+  int n_max = 1;
+  uint64_t N = 0, RR = 0, e_cap = 0, tiles = 0;
+  std::vector<CloudInfo> ci(C);
+  std::vector<uint32_t> tile_off(C + 1, 0);
+  for (int c = 0; c < C; ++c) {
+    const int n = (int)ns[c];
+    n_max = std::max(n_max, n);
+    ci[c].n = n;
+    ci[c].voff = (uint32_t)N;
+    ci[c].roff = RR;
+    ci[c].eoff = 0;
+    ci[c].m = 0;
+    ci[c].t_eff = 0;
+    ci[c].pad = 0;
+    N += n;
+    RR += (uint64_t)n * n;
+    e_cap += (uint64_t)n * (n - 1) / 2;
+    const uint64_t nb = (n + 31) / 32;
+    tile_off[c] = (uint32_t)tiles;
+    tiles += nb * (nb + 1) / 2;
+  }
+  tile_off[C] = (uint32_t)tiles;
+  if (N > 0xFFFFFFF0ull || e_cap > 0xFFFFFFF0ull || tiles > 0x7FFFFFFFull) return RIPS_ERR_OVERFLOW;
+  const int cb = C > 1 ? bit_width64((uint64_t)C - 1) : 0;
+  const int eb = bits_of_count(host_binom(n_max, 2));
+  if (cb + 32 + eb > 64) return RIPS_ERR_OVERFLOW;
+  CR(ensure(w.clouds, (size_t)C * sizeof(CloudInfo)));
+  CR(ensure(w.tileoff, (size_t)(C + 1) * 4));
+  CR(ensure(w.vcloud, (size_t)N * 4));
+  CR(ensure(w.ccounts, (size_t)(C + 1) * 4));
+  CloudInfo* dclouds = P<CloudInfo>(w.clouds);
+  CK(cudaMemcpyAsync(dclouds, ci.data(), (size_t)C * sizeof(CloudInfo), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(w.tileoff.p, tile_off.data(), (size_t)(C + 1) * 4, cudaMemcpyHostToDevice, s));
+
   // ---------------- prologue
-  const uint64_t e_cap = (uint64_t)n * (n - 1) / 2;
-  CR(ensure(w.rowmax, (size_t)n * 4));
+  CR(ensure(w.rowmax, (size_t)N * 4));
   CR(ensure(w.teff, 16));
   CR(ensure(w.err, 16));
   CR(ensure(w.ecount, 16));
   CR(ensure(w.ekeys, e_cap * 8));
   CR(ensure(w.ekeys_alt, e_cap * 8));
-  CK(cudaMemsetAsync(w.rowmax.p, 0, (size_t)n * 4, s));
+  CK(cudaMemsetAsync(w.rowmax.p, 0, (size_t)N * 4, s));
   CK(cudaMemsetAsync(w.err.p, 0, 16, s));
   CK(cudaMemsetAsync(w.ecount.p, 0, 16, s));
+  CK(cudaMemsetAsync(w.ccounts.p, 0, (size_t)(C + 1) * 4, s));
   {
     KTimer kt(w, RIPS_K_PROLOGUE, s);
-    if (n > 1) CK(launch_validate_rowmax(dD, n, P<uint32_t>(w.rowmax), P<uint32_t>(w.err), s));
-    CK(launch_threshold(P<uint32_t>(w.rowmax), n, threshold, P<float>(w.teff), s));
-    if (n > 1)
-      CK(launch_edge_keys(dD, n, P<float>(w.teff), P<uint64_t>(w.ekeys), P<uint32_t>(w.ecount), (uint32_t)e_cap, s));
+    CK(launch_cloud_vertices(dclouds, C, P<uint32_t>(w.vcloud), s));
+    CK(launch_validate_rowmax(dD, dclouds, P<uint32_t>(w.tileoff), C, (uint32_t)tiles, P<uint32_t>(w.rowmax),
+                              P<uint32_t>(w.err), s));
+    CK(launch_threshold(P<uint32_t>(w.rowmax), dclouds, C, threshold, s));
+    CK(launch_edge_keys(dD, dclouds, P<uint32_t>(w.vcloud), (uint32_t)N, eb, P<uint64_t>(w.ekeys),
+                        P<uint32_t>(w.ecount), P<uint32_t>(w.ccounts), (uint32_t)e_cap, s));
   }
+  std::vector<uint32_t> ccount(C);
   CK(cudaMemcpyAsync(&hp->u32[0], w.ecount.p, 4, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(&hp->u32[1], w.err.p, 4, cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(&hp->f32[0], w.teff.p, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(ccount.data(), w.ccounts.p, (size_t)C * 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(ci.data(), dclouds, (size_t)C * sizeof(CloudInfo), cudaMemcpyDeviceToHost, s));
   CR(sync_read(w, s));
   if (hp->u32[1] & ERRF_BAD_INPUT) return RIPS_ERR_BAD_ARG;
   const uint32_t m = hp->u32[0];
-  out.t_eff = hp->f32[0];
+  out.t_eff.resize(C);
+  {
+    uint32_t acc = 0;
+    for (int c = 0; c < C; ++c) {
+      ci[c].eoff = acc;
+      ci[c].m = ccount[c];
+      acc += ccount[c];
+      out.t_eff[c] = ci[c].t_eff;
+    }
+  }
+  CK(cudaMemcpyAsync(dclouds, ci.data(), (size_t)C * sizeof(CloudInfo), cudaMemcpyHostToDevice, s));
 
-  // sort edges: (diameter bits, inverted index) ascending = filtration order
-  CR(ensure(w.sorttmp, std::max(sort_temp_bytes(m), scan_temp_bytes(m > (uint32_t)n + 1 ? m : n + 1))));
+  // sort edges: (cloud, length bits, inverted index) ascending = each cloud's filtration order
+  CR(ensure(w.sorttmp, std::max(sort_temp_bytes(m), scan_temp_bytes((uint32_t)std::max<uint64_t>(m, N + 1)))));
   bool alt = false;
   {
     KTimer kt(w, RIPS_K_EDGE_SORT, s);
-    CK(radix_sort_u64(P<uint64_t>(w.ekeys), P<uint64_t>(w.ekeys_alt), nullptr, nullptr, m, 64, w.sorttmp.p,
-                      w.sorttmp.cap, &alt, s));
+    CK(radix_sort_u64(P<uint64_t>(w.ekeys), P<uint64_t>(w.ekeys_alt), nullptr, nullptr, m, cb + 32 + eb,
+                      w.sorttmp.p, w.sorttmp.cap, &alt, s));
   }
   const uint64_t* keys = alt ? P<uint64_t>(w.ekeys_alt) : P<uint64_t>(w.ekeys);
-  uint64_t* keys_other = alt ? P<uint64_t>(w.ekeys) : P<uint64_t>(w.ekeys_alt);
 
   CR(ensure(w.eflags, (size_t)(m + 1) * 4));
   CR(ensure(w.erank, (size_t)(m + 1) * 4));
   CR(ensure(w.rvalue, (size_t)(m + 1) * 4));
-  KTimer* kt_pro = new KTimer(w, RIPS_K_PROLOGUE, s);
-  CK(launch_assign_ranks(keys, m, P<uint32_t>(w.eflags), (uint32_t*)w.sorttmp.p, w.sorttmp.cap,
-                         P<uint32_t>(w.erank), P<float>(w.rvalue), &P<uint32_t>(w.ecount)[1], s));
-  CR(ensure(w.R, (size_t)n * n * 4));
-  CK(launch_fill_rank_matrix(keys, P<uint32_t>(w.erank), m, n, P<uint32_t>(w.R), s));
-  CR(ensure(w.deg, (size_t)(n + 2) * 4));
-  CK(cudaMemsetAsync(w.deg.p, 0, (size_t)(n + 2) * 4, s));
-  CK(launch_neighbor_counts(P<uint32_t>(w.R), n, P<uint32_t>(w.deg), s));
-  CK(launch_exclusive_scan(P<uint32_t>(w.deg), P<uint32_t>(w.deg), (uint32_t)n + 1, w.sorttmp.p,
-                           &P<uint32_t>(w.ecount)[2], s));
-  delete kt_pro;
-  CK(cudaMemcpyAsync(&hp->u32[2], (char*)w.ecount.p + 4, 8, cudaMemcpyDeviceToHost, s));
+  CR(ensure(w.R, RR * 4));
+  CR(ensure(w.deg, (size_t)(N + 2) * 4));
+  {
+    KTimer kt(w, RIPS_K_PROLOGUE, s);
+    CK(launch_assign_ranks(keys, m, eb, P<uint32_t>(w.eflags), (uint32_t*)w.sorttmp.p, P<uint32_t>(w.erank),
+                           P<float>(w.rvalue), &P<uint32_t>(w.ecount)[1], s));
+    CK(cudaMemsetAsync(w.R.p, 0xFF, RR * 4, s));
+    CK(launch_fill_rank_matrix(keys, P<uint32_t>(w.erank), m, eb, dclouds, P<uint32_t>(w.R), s));
+    CK(cudaMemsetAsync(w.deg.p, 0, (size_t)(N + 2) * 4, s));
+    CK(launch_neighbor_counts(P<uint32_t>(w.R), dclouds, P<uint32_t>(w.vcloud), (uint32_t)N, P<uint32_t>(w.deg),
+                              &P<uint32_t>(w.ecount)[3], s));
+    CK(launch_exclusive_scan(P<uint32_t>(w.deg), P<uint32_t>(w.deg), (uint32_t)N + 1, w.sorttmp.p,
+                             &P<uint32_t>(w.ecount)[2], s));
+  }
+  CK(cudaMemcpyAsync(&hp->u32[2], (char*)w.ecount.p + 4, 12, cudaMemcpyDeviceToHost, s));
   CR(sync_read(w, s));
   const uint32_t num_ranks = hp->u32[2];
   const uint32_t nbr_total = hp->u32[3];
+  const uint32_t max_deg = hp->u32[4];
   CR(ensure(w.nbr, (size_t)nbr_total * 4));
-  CR(ensure(w.binom, (size_t)(kmax + 1) * (n + 1) * 8));
+  CR(ensure(w.binom, (size_t)(kmax + 1) * (n_max + 1) * 8));
   {
     KTimer kt(w, RIPS_K_PROLOGUE, s);
-    CK(launch_neighbor_fill(P<uint32_t>(w.R), n, P<uint32_t>(w.deg), P<uint32_t>(w.nbr), s));
-    CK(launch_binomial_table(P<uint64_t>(w.binom), n, kmax, s));
+    CK(launch_neighbor_fill(P<uint32_t>(w.R), dclouds, P<uint32_t>(w.vcloud), (uint32_t)N, P<uint32_t>(w.deg),
+                            P<uint32_t>(w.nbr), s));
+    CK(launch_binomial_table(P<uint64_t>(w.binom), n_max, kmax, s));
   }
 
   // ---------------- H0
-  const uint64_t bar_need = (uint64_t)*h_nbars_io + (uint64_t)n + 16;
-  CR(grow_keep(w.bars, bar_need * sizeof(rips_bar_t), (size_t)*h_nbars_io * sizeof(rips_bar_t), s));
+  CR(grow_keep(w.bars, ((size_t)N + 16) * sizeof(rips_bar_t), 0, s));
   CR(ensure(w.eu, (size_t)(m + 1) * 4));
   CR(ensure(w.ev, (size_t)(m + 1) * 4));
-  CR(ensure(w.comp, (size_t)n * 4));
-  CR(ensure(w.best, (size_t)n * 4));
-  CR(ensure(w.parent, (size_t)n * 4));
-  CR(ensure(w.gtop, (size_t)n * 4));
   CR(ensure(w.inforest, (size_t)m + 1));
-  CR(ensure(w.fpos, (size_t)n * 4));
-  CR(ensure(w.nf, 16));
   CR(ensure(w.nbars, 16));
-  CR(ensure(w.stats, (size_t)(dim_max + 1) * 16 * 8));
-  CK(cudaMemsetAsync(w.stats.p, 0, (size_t)(dim_max + 1) * 16 * 8, s));
-  hp->u32[4] = *h_nbars_io;
-  CK(cudaMemcpyAsync(w.nbars.p, &hp->u32[4], 4, cudaMemcpyHostToDevice, s));
+  CR(ensure(w.stats, (size_t)C * SPC * 8));
+  CK(cudaMemsetAsync(w.stats.p, 0, (size_t)C * SPC * 8, s));
+  CK(cudaMemsetAsync(w.nbars.p, 0, 4, s));
   unsigned long long* dstats = P<unsigned long long>(w.stats);
-  KTimer* kt_h0 = new KTimer(w, RIPS_K_H0, s);
-  CK(run_h0(n, keys, m, P<uint32_t>(w.eu), P<uint32_t>(w.ev), P<uint32_t>(w.comp), P<uint32_t>(w.best),
-            P<uint32_t>(w.parent), P<uint8_t>(w.inforest), P<uint32_t>(w.eflags), P<uint32_t>(w.fpos), w.sorttmp.p,
-            P<uint32_t>(w.nf), P<uint32_t>(w.gtop), P<rips_bar_t>(w.bars), P<uint32_t>(w.nbars),
-            (uint32_t)(w.bars.cap / sizeof(rips_bar_t)), cloud, dstats, P<uint32_t>(w.err), s));
-  delete kt_h0;
+  {
+    KTimer kt(w, RIPS_K_H0, s);
+    if (h0_blocks_fit(n_max)) {
+      CK(launch_h0_blocks(dclouds, C, n_max, keys, eb, P<uint32_t>(w.eu), P<uint32_t>(w.ev), m,
+                          P<uint8_t>(w.inforest), P<rips_bar_t>(w.bars), P<uint32_t>(w.nbars),
+                          (uint32_t)(w.bars.cap / sizeof(rips_bar_t)), dstats, SPC, P<uint32_t>(w.err), s));
+    } else {
+      if (C != 1) return RIPS_ERR_BAD_ARG;
+      const int n = n_max;
+      CR(ensure(w.comp, (size_t)n * 4));
+      CR(ensure(w.best, (size_t)n * 4));
+      CR(ensure(w.parent, (size_t)n * 4));
+      CR(ensure(w.gtop, (size_t)n * 4));
+      CR(ensure(w.fpos, (size_t)n * 4));
+      CR(ensure(w.nf, 16));
+      CK(run_h0_large(n, keys, m, eb, P<uint32_t>(w.eu), P<uint32_t>(w.ev), P<uint32_t>(w.comp), P<uint32_t>(w.best),
+                      P<uint32_t>(w.parent), P<uint8_t>(w.inforest), P<uint32_t>(w.eflags), P<uint32_t>(w.fpos),
+                      w.sorttmp.p, P<uint32_t>(w.nf), P<uint32_t>(w.gtop), P<rips_bar_t>(w.bars),
+                      P<uint32_t>(w.nbars), (uint32_t)(w.bars.cap / sizeof(rips_bar_t)), dstats, P<uint32_t>(w.err),
+                      s));
+    }
+  }
   if (w.events) CK(cudaEventRecord(w.tev[1], s));
 
   // ---------------- dimensions 1..dim_max
   const int rank_bits = bit_width64(num_ranks ? num_ranks - 1 : 0);
   uint32_t ns_prev = 0;  // size of the (d-1)-simplex list in sidx[cur^1]
+  int prev_col_bits = 0;
   int cur = 0;
   uint64_t* prev_tkeys = nullptr;
   uint64_t prev_tmask = 0;
   for (int d = 1; d <= dim_max; ++d) {
     DimArgs a;
-    a.n = n;
     a.d = d;
+    a.nclouds = C;
+    a.clouds = dclouds;
     a.R = P<uint32_t>(w.R);
     a.nbr_off = P<uint32_t>(w.deg);
     a.nbr = P<uint32_t>(w.nbr);
     a.binom = P<uint64_t>(w.binom);
+    a.bn = n_max;
     a.kmax = kmax;
-    a.smem_binom = (size_t)(kmax + 1) * (n + 1) * 8 <= 48 * 1024;
+    a.smem_binom = (size_t)(kmax + 1) * (n_max + 1) * 8 <= 48 * 1024;
     a.p = p;
-    a.col_bits = std::max(1, bit_width64(host_binom(n, d + 1) ? host_binom(n, d + 1) - 1 : 0));
-    a.row_bits = std::max(1, bit_width64(host_binom(n, d + 2) ? host_binom(n, d + 2) - 1 : 0));
+    a.col_bits = bits_of_count(host_binom(n_max, d + 1));
+    a.row_bits = bits_of_count(host_binom(n_max, d + 2));
+    a.rank_bits = rank_bits;
     a.rank_max = num_ranks ? num_ranks - 1 : 0;
     a.err = P<uint32_t>(w.err);
-    if (rank_bits + a.row_bits > 64 || rank_bits + a.col_bits > 64) return RIPS_ERR_OVERFLOW;
-    unsigned long long* st = dstats + d * 16;
+    if (rank_bits + a.row_bits > 63 || cb + rank_bits + a.col_bits > 64 || cb + a.row_bits > 64)
+      return RIPS_ERR_OVERFLOW;
+    unsigned long long* st = dstats + d * 16;  // cloud c: st + c * SPC
 
     // d-simplices
-    uint32_t ns = 0;
+    uint32_t nsd = 0;
     if (d == 1) {
-      ns = m;
+      nsd = m;
       CR(ensure(w.sidx[cur], (size_t)(m + 1) * 8));
       CR(ensure(w.srank[cur], (size_t)(m + 1) * 4));
-      CK(launch_edges_to_simplices(keys, P<uint32_t>(w.erank), m, P<uint64_t>(w.sidx[cur]), P<uint32_t>(w.srank[cur]),
-                                   s));
+      CK(launch_edges_to_simplices(keys, P<uint32_t>(w.erank), m, eb, a.col_bits, P<uint64_t>(w.sidx[cur]),
+                                   P<uint32_t>(w.srank[cur]), s));
     } else {
       CR(ensure(w.scount, 16));
       const int pv = cur ^ 1;
@@ -389,44 +464,51 @@ int run_cloud(Workspace& w, const float* dD, int n, int dim_max, float threshold
         unsigned long long cap = w.sidx[cur].cap / 8;
         if (w.srank[cur].cap / 4 < cap) cap = w.srank[cur].cap / 4;
         CK(cudaMemsetAsync(w.scount.p, 0, 8, s));
-        KTimer kt(w, RIPS_K_ENUMERATE, s);
-        CK(launch_enumerate(a, P<uint64_t>(w.sidx[pv]), P<uint32_t>(w.srank[pv]), ns_prev, P<uint64_t>(w.sidx[cur]),
-                            P<uint32_t>(w.srank[cur]), P<unsigned long long>(w.scount), cap, s));
+        {
+          KTimer kt(w, RIPS_K_ENUMERATE, s);
+          CK(launch_enumerate(a, P<uint64_t>(w.sidx[pv]), P<uint32_t>(w.srank[pv]), ns_prev, prev_col_bits,
+                              P<uint64_t>(w.sidx[cur]), P<uint32_t>(w.srank[cur]),
+                              P<unsigned long long>(w.scount), cap, s));
+        }
         CK(cudaMemcpyAsync(&hp->u64[0], w.scount.p, 8, cudaMemcpyDeviceToHost, s));
         CR(sync_read(w, s));
         const unsigned long long got = hp->u64[0];
         if (got > 0xFFFFFFF0ull) return RIPS_ERR_OVERFLOW;
         if (got <= cap) {
-          ns = (uint32_t)got;
+          nsd = (uint32_t)got;
           break;
         }
         CR(ensure(w.sidx[cur], got * 8));
         CR(ensure(w.srank[cur], got * 4));
       }
     }
-    out.stats[d].simplices = ns;
 
     // apparent pairs, clearing, compaction
-    CR(ensure(w.ckeys, (size_t)(ns + 1) * 8));
-    CR(ensure(w.ckeys_alt, (size_t)(ns + 1) * 8));
+    CR(ensure(w.ckeys, (size_t)(nsd + 1) * 8));
+    CR(ensure(w.ckeys_alt, (size_t)(nsd + 1) * 8));
     CR(ensure(w.ccount, 16));
     CK(cudaMemsetAsync(w.ccount.p, 0, 16, s));
     {
       KTimer kt(w, RIPS_K_APPARENT, s);
-      CK(launch_test(a, P<uint64_t>(w.sidx[cur]), P<uint32_t>(w.srank[cur]), ns, P<uint8_t>(w.inforest), prev_tkeys,
-                     prev_tmask, P<uint64_t>(w.ckeys), P<uint32_t>(w.ccount), ns + 1, st + 4, s));
+      CK(launch_test(a, P<uint64_t>(w.sidx[cur]), P<uint32_t>(w.srank[cur]), nsd, P<uint8_t>(w.inforest), prev_tkeys,
+                     prev_tmask, P<uint64_t>(w.ckeys), P<uint32_t>(w.ccount), nsd + 1, st, SPC, s));
     }
     CK(cudaMemcpyAsync(&hp->u32[5], w.ccount.p, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&hp->u32[10], w.nbars.p, 4, cudaMemcpyDeviceToHost, s));
     CR(sync_read(w, s));
     const uint32_t M = hp->u32[5];
     // processing order
     CR(ensure(w.sorttmp, std::max(w.sorttmp.cap, sort_temp_bytes(M + 1))));
     bool calt = false;
-    KTimer* kt_cs = new KTimer(w, RIPS_K_COL_SORT, s);
-    CK(radix_sort_u64(P<uint64_t>(w.ckeys), P<uint64_t>(w.ckeys_alt), nullptr, nullptr, M, rank_bits + a.col_bits,
-                      w.sorttmp.p, w.sorttmp.cap, &calt, s));
-    delete kt_cs;
+    {
+      KTimer kt(w, RIPS_K_COL_SORT, s);
+      CK(radix_sort_u64(P<uint64_t>(w.ckeys), P<uint64_t>(w.ckeys_alt), nullptr, nullptr, M,
+                        cb + rank_bits + a.col_bits, w.sorttmp.p, w.sorttmp.cap, &calt, s));
+    }
     const uint64_t* ckeys = calt ? P<uint64_t>(w.ckeys_alt) : P<uint64_t>(w.ckeys);
+    // bars of this dimension are appended after the current count
+    CR(grow_keep(w.bars, ((size_t)hp->u32[10] + M + 16) * sizeof(rips_bar_t),
+                 (size_t)hp->u32[10] * sizeof(rips_bar_t), s));
 
     // reduction
     const int tb = cur;  // table for this dimension (the other one holds d-1)
@@ -435,139 +517,122 @@ int run_cloud(Workspace& w, const float* dD, int n, int dim_max, float threshold
     CR(ensure(w.tvals[tb], (size_t)tcap * 4));
     CR(ensure(w.piv_key, (size_t)(M + 1) * 8));
     CR(ensure(w.piv_coef, (size_t)(M + 1) * 4));
-    CR(ensure(w.v_off, (size_t)(M + 1) * 4));
-    CR(ensure(w.v_len, (size_t)(M + 1) * 4));
+    CR(ensure(w.r_off, (size_t)(M + 1) * 8));
+    CR(ensure(w.r_len, (size_t)(M + 1) * 4));
     CR(ensure(w.reduced, (size_t)(M + 1)));
     CR(ensure(w.claim, (size_t)(M + 1) * 4));
     CR(ensure(w.reduce, (size_t)(M + 1) * 4));
     CR(ensure(w.lists, 64));
-    CR(ensure(w.v_top, 16));
-    size_t vcap = std::max<size_t>(w.v_cap, 4 * (size_t)M + 4096);
-    int red_rc = RIPS_OK;
-    for (int attempt = 0; attempt < 6; ++attempt) {
-      CR(ensure(w.v_idx, vcap * 8));
-      CR(ensure(w.v_rank, vcap * 4));
-      CR(ensure(w.v_coef, vcap * 4));
-      w.v_cap = vcap;
+    CR(ensure(w.r_top, 16));
+    // a generated coboundary holds at most max_deg entries (sorted in a power-of-two buffer)
+    const int blocks = M ? reduction_blocks(a, M) : 1;
+    if (blocks < 1) return RIPS_ERR_CUDA;
+    uint32_t slice = 32;
+    while (slice < max_deg + 1) slice <<= 1;
+    size_t rcap = std::max<size_t>(w.r_cap, std::max<size_t>(16 * (size_t)M, (size_t)1 << 22));
+    bool done = false;
+    for (int attempt = 0; attempt < 6 && !done; ++attempt) {
+      CR(ensure(w.r_key, rcap * 8));
+      CR(ensure(w.r_coef, rcap * 4));
+      w.r_cap = rcap;
       CK(cudaMemsetAsync(w.tkeys[tb].p, 0xFF, (size_t)tcap * 8, s));
       CK(cudaMemsetAsync(w.tvals[tb].p, 0xFF, (size_t)tcap * 4, s));
       CK(cudaMemsetAsync(w.lists.p, 0, 64, s));
-      CK(cudaMemsetAsync(w.v_top.p, 0, 16, s));
-      CK(cudaMemsetAsync(st + 9, 0, 8, s));
+      CK(cudaMemsetAsync(w.r_top.p, 0, 16, s));
       uint32_t* counts = P<uint32_t>(w.lists);
       RedState rs;
       rs.col_keys = ckeys;
       rs.ncols = M;
       rs.piv_key = P<uint64_t>(w.piv_key);
       rs.piv_coef = P<uint32_t>(w.piv_coef);
-      rs.v_off = P<uint32_t>(w.v_off);
-      rs.v_len = P<uint32_t>(w.v_len);
       rs.reduced = P<uint8_t>(w.reduced);
-      rs.v_idx = P<uint64_t>(w.v_idx);
-      rs.v_rank = P<uint32_t>(w.v_rank);
-      rs.v_coef = P<uint32_t>(w.v_coef);
-      rs.v_top = P<unsigned long long>(w.v_top);
-      rs.v_cap = vcap;
+      rs.r_key = P<uint64_t>(w.r_key);
+      rs.r_coef = P<uint32_t>(w.r_coef);
+      rs.r_off = P<unsigned long long>(w.r_off);
+      rs.r_len = P<uint32_t>(w.r_len);
+      rs.r_top = P<unsigned long long>(w.r_top);
+      rs.r_cap = rcap;
+      rs.scr_slice = slice;
       rs.t_keys = P<uint64_t>(w.tkeys[tb]);
       rs.t_vals = P<uint32_t>(w.tvals[tb]);
       rs.t_mask = tcap - 1;
       rs.claim_list = P<uint32_t>(w.claim);
       rs.reduce_list = P<uint32_t>(w.reduce);
-      rs.steps = st + 9;
+      rs.steps = P<unsigned long long>(w.lists) + 4;
+      rs.compacted = P<unsigned long long>(w.lists) + 5;
+      rs.max_chain = counts + 7;
       rs.err = P<uint32_t>(w.err);
-      // claim counter at counts[0], reduce counter at counts[1]
-      rs.claim_count = counts + 0;
-      rs.reduce_count = counts + 1;
       {
-        KTimer kt(w, RIPS_K_PIVOT_INIT, s);
-        CK(launch_init(a, rs, s));
+        KTimer kt(w, RIPS_K_REDUCE, s);
+        CK(launch_reduction(a, rs, blocks, counts, s));
       }
-      uint32_t rounds = 0;
-      bool arena_full = false;
-      for (;;) {
-        CK(cudaMemcpyAsync(&hp->u32[6], w.lists.p, 8, cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(&hp->u32[8], w.err.p, 4, cudaMemcpyDeviceToHost, s));
-        CR(sync_read(w, s));
-        if (hp->u32[8] & ERRF_ARENA) {
-          arena_full = true;
-          break;
-        }
-        if (int e = map_device_error(hp->u32[8])) return e;
-        const uint32_t nclaim = hp->u32[6];
-        if (nclaim == 0) break;
-        if (++rounds > 1000000u) return RIPS_ERR_DEVICE_TIMEOUT;
-        // claims: claim list -> reduce list
-        CK(cudaMemsetAsync(counts + 1, 0, 4, s));
-        {
-          KTimer kt(w, RIPS_K_REDUCE, s);
-          CK(launch_claim(a, rs, nclaim, s));
-        }
-        CK(cudaMemsetAsync(counts + 0, 0, 4, s));
-        CK(cudaMemcpyAsync(&hp->u32[7], counts + 1, 4, cudaMemcpyDeviceToHost, s));
-        CR(sync_read(w, s));
-        const uint32_t nred = hp->u32[7];
-        // reductions: reduce list -> claim list
-        {
-          KTimer kt(w, RIPS_K_REDUCE, s);
-          CK(launch_reduce(a, rs, nred, s));
-        }
-      }
-      if (arena_full) {
+      CK(cudaMemcpyAsync(&hp->u32[6], counts + 6, 4, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(&hp->u32[8], w.err.p, 4, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(&hp->u64[1], rs.steps, 16, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(&hp->u32[9], counts + 7, 4, cudaMemcpyDeviceToHost, s));
+      CR(sync_read(w, s));
+      if (hp->u32[8] & ERRF_ARENA) {
         // start this dimension's reduction over with a larger arena
-        hp->u32[9] = 0;
         CK(cudaMemsetAsync(w.err.p, 0, 4, s));
-        vcap *= 4;
+        rcap *= 4;
         continue;
       }
-      out.stats[d].rounds = rounds;
-      // bars are appended after the current count: make sure room exists
-      {
-        CK(cudaMemcpyAsync(&hp->u32[10], w.nbars.p, 4, cudaMemcpyDeviceToHost, s));
-        CR(sync_read(w, s));
-        const size_t need = ((size_t)hp->u32[10] + M + 16) * sizeof(rips_bar_t);
-        CR(grow_keep(w.bars, need, (size_t)hp->u32[10] * sizeof(rips_bar_t), s));
+      if (int e = map_device_error(hp->u32[8])) return e;
+      out.stats.resize((size_t)C * (dim_max + 1));
+      // rounds and steps are properties of the whole batch's reduction
+      for (int c = 0; c < C; ++c) {
+        out.stats[(size_t)c * (dim_max + 1) + d].rounds = hp->u32[6];
+        out.stats[(size_t)c * (dim_max + 1) + d].reduction_steps = (int64_t)hp->u64[1];
+        out.stats[(size_t)c * (dim_max + 1) + d].longest_chain = hp->u32[9];
+        out.stats[(size_t)c * (dim_max + 1) + d].compacted_entries = (int64_t)hp->u64[2];
       }
       {
         KTimer kt(w, RIPS_K_READOUT, s);
-        CK(launch_readout(a, rs, P<float>(w.rvalue), cloud, P<rips_bar_t>(w.bars), P<uint32_t>(w.nbars),
-                          (uint32_t)(w.bars.cap / sizeof(rips_bar_t)), st, s));
+        CK(launch_readout(a, rs, P<float>(w.rvalue), P<rips_bar_t>(w.bars), P<uint32_t>(w.nbars),
+                          (uint32_t)(w.bars.cap / sizeof(rips_bar_t)), st, SPC, s));
       }
-      red_rc = RIPS_OK;
-      break;
+      done = true;
     }
-    CR(red_rc);
-    out.stats[d].columns = M;
+    if (!done) return RIPS_ERR_OOM;
     prev_tkeys = P<uint64_t>(w.tkeys[tb]);
     prev_tmask = tcap - 1;
-    ns_prev = ns;
+    ns_prev = nsd;
+    prev_col_bits = a.col_bits;
     cur ^= 1;
     if (w.events && d + 1 < 16) CK(cudaEventRecord(w.tev[d + 1], s));
   }
 
   // statistics and bar count
-  CK(cudaMemcpyAsync(hp->u64, dstats, (size_t)(dim_max + 1) * 16 * 8, cudaMemcpyDeviceToHost, s));
+  std::vector<unsigned long long> hstats((size_t)C * SPC);
+  CK(cudaMemcpyAsync(hstats.data(), dstats, (size_t)C * SPC * 8, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(&hp->u32[11], w.nbars.p, 4, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(&hp->u32[12], w.err.p, 4, cudaMemcpyDeviceToHost, s));
   CR(sync_read(w, s));
   if (int e = map_device_error(hp->u32[12])) return e;
-  *h_nbars_io = hp->u32[11];
-  // dimension 0 statistics from the H0 kernel (pairs, zero, essential)
-  out.stats[0].simplices = n;
-  out.stats[0].columns = n;
-  out.stats[0].pairs = (int64_t)hp->u64[0];
-  out.stats[0].zero_pairs = (int64_t)hp->u64[1];
-  out.stats[0].essential = (int64_t)hp->u64[2];
-  out.stats[0].emergent = 0;
-  for (int d = 1; d <= dim_max; ++d) {
-    const unsigned long long* q = hp->u64 + d * 16;
-    out.stats[d].pairs = (int64_t)q[0];
-    out.stats[d].zero_pairs = (int64_t)q[1];
-    out.stats[d].essential = (int64_t)q[2];
-    out.stats[d].emergent = (int64_t)q[3];
-    out.stats[d].apparent_cofacet = (int64_t)q[4];
-    out.stats[d].apparent_facet = (int64_t)q[5];
-    out.stats[d].cleared = (int64_t)q[6];
-    out.stats[d].reduction_steps = (int64_t)q[9];
+  out.nbars = hp->u32[11];
+  out.stats.resize((size_t)C * (dim_max + 1));
+  for (int c = 0; c < C; ++c) {
+    const unsigned long long* q0 = hstats.data() + (size_t)c * SPC;
+    rips_stats_t& s0 = out.stats[(size_t)c * (dim_max + 1)];
+    s0.simplices = ns[c];
+    s0.columns = ns[c];
+    s0.pairs = (int64_t)q0[0];
+    s0.zero_pairs = (int64_t)q0[1];
+    s0.essential = (int64_t)q0[2];
+    for (int d = 1; d <= dim_max; ++d) {
+      const unsigned long long* q = q0 + d * 16;
+      rips_stats_t& sd = out.stats[(size_t)c * (dim_max + 1) + d];
+      sd.pairs = (int64_t)q[0];
+      sd.zero_pairs = (int64_t)q[1];
+      sd.essential = (int64_t)q[2];
+      sd.emergent = (int64_t)q[3];
+      sd.apparent_cofacet = (int64_t)q[4];
+      sd.apparent_facet = (int64_t)q[5];
+      sd.cleared = (int64_t)q[6];
+      // columns = pairs found by the reduction + essential classes; simplices = all four categories
+      sd.columns = sd.pairs + sd.essential;
+      sd.simplices = sd.apparent_cofacet + sd.apparent_facet + sd.cleared + sd.columns;
+    }
   }
   for (size_t q = 0; q < w.kev_used; ++q) {
     float ms = 0;
@@ -616,6 +681,16 @@ void index_result(rips_result* r) {
   for (size_t i = 0; i < cnt.size(); ++i) r->offsets[i + 1] = r->offsets[i] + cnt[i];
 }
 
+void fill_result(rips_result* r, const BatchOut& bo) {
+  r->thresholds = bo.t_eff;
+  r->stats = bo.stats;
+  r->phase_ms = bo.phase_ms;
+  for (int q = 0; q < RIPS_KERNEL_CLASSES; ++q) {
+    r->kernel_ms[q] = bo.kernel_ms[q];
+    r->kernel_launches[q] = bo.kernel_regions[q];
+  }
+}
+
 // caller holds w.mu
 int barcodes_locked(Workspace& w, const float* dD, int64_t n, int32_t dim_max, float threshold, uint32_t p,
                     cudaStream_t s, rips_result_t** out) {
@@ -623,24 +698,18 @@ int barcodes_locked(Workspace& w, const float* dD, int64_t n, int32_t dim_max, f
   if (!r) return RIPS_ERR_OOM;
   r->clouds = 1;
   r->dim_max = dim_max;
-  uint32_t nb = 0;
-  CloudOut co;
-  int rc = run_cloud(w, dD, (int)n, dim_max, threshold, p, 0, s, &nb, co);
+  BatchOut bo;
+  std::vector<int64_t> ns{n};
+  int rc = run_batch(w, dD, ns, dim_max, threshold, p, s, bo);
   if (rc == RIPS_OK) {
     const int sbits = std::max(1, bit_width64(host_binom((uint64_t)n, dim_max + 1)));
-    rc = finish_bars(w, nb, sbits, 0, s, r->bars);
+    rc = finish_bars(w, bo.nbars, sbits, 0, s, r->bars);
   }
   if (rc != RIPS_OK) {
     delete r;
     return rc;
   }
-  r->thresholds.push_back(co.t_eff);
-  r->stats = co.stats;
-  r->phase_ms = co.phase_ms;
-  for (int q = 0; q < RIPS_KERNEL_CLASSES; ++q) {
-    r->kernel_ms[q] = co.kernel_ms[q];
-    r->kernel_launches[q] = co.kernel_regions[q];
-  }
+  fill_result(r, bo);
   r->npoints.push_back(n);
   r->point_offsets = {0, n};
   index_result(r);
@@ -657,6 +726,7 @@ Workspace* current_workspace() {
   return workspace(dev);
 }
 
+// all clouds' distance matrices in one launch, then one pipeline for the batch
 int batched_locked(Workspace& w, const float* d_points, const int64_t* offsets, int32_t batch, int32_t k,
                    int32_t dim_max, float threshold, uint32_t p, cudaStream_t s, rips_result_t** out) {
   rips_result* r = new (std::nothrow) rips_result();
@@ -664,37 +734,46 @@ int batched_locked(Workspace& w, const float* d_points, const int64_t* offsets, 
   r->clouds = batch;
   r->dim_max = dim_max;
   r->k = k;
-  uint32_t nb = 0;
-  int rc = RIPS_OK;
+  std::vector<int64_t> ns(batch);
+  std::vector<CloudInfo> ci(batch);
+  std::vector<uint32_t> row_off(batch + 1, 0);
+  uint64_t RR = 0, rows = 0;
   int64_t nmax = 1;
-  for (int32_t c = 0; c < batch; ++c) nmax = std::max<int64_t>(nmax, offsets[c + 1] - offsets[c]);
-  rc = ensure(w.cdist, (size_t)nmax * nmax * 4);
-  for (int32_t c = 0; rc == RIPS_OK && c < batch; ++c) {
-    const int64_t n = offsets[c + 1] - offsets[c];
-    if (launch_distance_matrix(d_points + (size_t)offsets[c] * k, (int)n, k, P<float>(w.cdist), s) != cudaSuccess) {
+  for (int32_t c = 0; c < batch; ++c) {
+    ns[c] = offsets[c + 1] - offsets[c];
+    nmax = std::max<int64_t>(nmax, ns[c]);
+    ci[c] = CloudInfo{(int)ns[c], (uint32_t)offsets[c], RR, 0, 0, 0.0f, 0};
+    RR += (uint64_t)ns[c] * ns[c];
+    row_off[c] = (uint32_t)rows;
+    rows += (ns[c] + 7) / 8;
+  }
+  row_off[batch] = (uint32_t)rows;
+  int rc = ensure(w.cdist, RR * 4);
+  if (rc == RIPS_OK) rc = ensure(w.clouds, (size_t)batch * sizeof(CloudInfo));
+  if (rc == RIPS_OK) rc = ensure(w.tileoff, (size_t)(batch + 1) * 4);
+  if (rc == RIPS_OK) {
+    if (cudaMemcpyAsync(w.clouds.p, ci.data(), (size_t)batch * sizeof(CloudInfo), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(w.tileoff.p, row_off.data(), (size_t)(batch + 1) * 4, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        launch_distance_matrices(d_points, k, P<CloudInfo>(w.clouds), P<uint32_t>(w.tileoff), batch, (uint32_t)rows,
+                                 P<float>(w.cdist), s) != cudaSuccess) {
       cudaGetLastError();
       rc = RIPS_ERR_CUDA;
-      break;
     }
-    CloudOut co;
-    rc = run_cloud(w, P<float>(w.cdist), (int)n, dim_max, threshold, p, c, s, &nb, co);
-    if (rc != RIPS_OK) break;
-    r->thresholds.push_back(co.t_eff);
-    r->stats.insert(r->stats.end(), co.stats.begin(), co.stats.end());
-    for (int q = 0; q < RIPS_KERNEL_CLASSES; ++q) {
-      r->kernel_ms[q] += co.kernel_ms[q];
-      r->kernel_launches[q] += co.kernel_regions[q];
-    }
-    r->npoints.push_back(n);
   }
+  BatchOut bo;
+  if (rc == RIPS_OK) rc = run_batch(w, P<float>(w.cdist), ns, dim_max, threshold, p, s, bo);
   if (rc == RIPS_OK) {
     const int sbits = std::max(1, bit_width64(host_binom((uint64_t)nmax, dim_max + 1)));
-    rc = finish_bars(w, nb, sbits, std::max(1, bit_width64((uint64_t)batch)), s, r->bars);
+    rc = finish_bars(w, bo.nbars, sbits, std::max(1, bit_width64((uint64_t)batch)), s, r->bars);
   }
   if (rc != RIPS_OK) {
     delete r;
     return rc;
   }
+  fill_result(r, bo);
+  r->npoints = ns;
   r->point_offsets.assign(offsets, offsets + batch + 1);
   index_result(r);
   *out = r;

@@ -98,23 +98,45 @@ __host__ __device__ __forceinline__ int bit_width64(uint64_t x) {
 // ------------------------------------------------------------------ host-side launchers
 // (defined in the .cu files; every launcher returns a cudaError_t of the launch)
 
-// rips_prologue.cu
+// ------------------------------------------------------------------ clouds
+// Every call works on a batch of independent clouds (one cloud for the
+// single-matrix entry points).  Cloud c owns n_c vertices; its n_c x n_c
+// distance and rank matrices start at element roff; its vertices are the global
+// rows voff .. voff + n_c - 1 of the neighbour-list CSR; its edges are the
+// positions eoff .. eoff + m_c - 1 of the sorted edge list.  A simplex is named
+// by (cloud << shift) | local combinatorial index.
+struct CloudInfo {
+  int n;
+  uint32_t voff;
+  uint64_t roff;
+  uint32_t eoff;
+  uint32_t m;
+  float t_eff;
+  uint32_t pad;
+};
+
+// rips_prologue.cu (all kernels run over every cloud of the batch)
 cudaError_t launch_binomial_table(uint64_t* tab, int n, int kmax, cudaStream_t s);
-cudaError_t launch_validate_rowmax(const float* D, int n, uint32_t* rowmax_bits, uint32_t* err,
-                                   cudaStream_t s);
-cudaError_t launch_threshold(const uint32_t* rowmax_bits, int n, float threshold, float* t_eff,
+cudaError_t launch_cloud_vertices(const CloudInfo* clouds, int nclouds, uint32_t* vcloud, cudaStream_t s);
+cudaError_t launch_validate_rowmax(const float* D, const CloudInfo* clouds, const uint32_t* tile_off, int nclouds,
+                                   uint32_t tiles, uint32_t* rowmax_bits, uint32_t* err, cudaStream_t s);
+cudaError_t launch_threshold(const uint32_t* rowmax_bits, CloudInfo* clouds, int nclouds, float threshold,
                              cudaStream_t s);
-cudaError_t launch_edge_keys(const float* D, int n, const float* t_eff, uint64_t* keys, uint32_t* count,
-                             uint32_t cap, cudaStream_t s);
-cudaError_t launch_assign_ranks(const uint64_t* sorted_keys, uint32_t num_edges, uint32_t* flags,
-                                uint32_t* scan_tmp, size_t scan_tmp_bytes, uint32_t* edge_rank,
-                                float* rank_value, uint32_t* num_ranks, cudaStream_t s);
-cudaError_t launch_fill_rank_matrix(const uint64_t* sorted_keys, const uint32_t* edge_rank,
-                                    uint32_t num_edges, int n, uint32_t* R, cudaStream_t s);
-cudaError_t launch_neighbor_counts(const uint32_t* R, int n, uint32_t* deg, cudaStream_t s);
-cudaError_t launch_neighbor_fill(const uint32_t* R, int n, const uint32_t* off, uint32_t* nbr,
-                                 cudaStream_t s);
+cudaError_t launch_edge_keys(const float* D, const CloudInfo* clouds, const uint32_t* vcloud, uint32_t nverts,
+                             int edge_bits, uint64_t* keys, uint32_t* count, uint32_t* cloud_count, uint32_t cap,
+                             cudaStream_t s);
+cudaError_t launch_assign_ranks(const uint64_t* sorted_keys, uint32_t num_edges, int edge_bits, uint32_t* flags,
+                                uint32_t* scan_tmp, uint32_t* edge_rank, float* rank_value, uint32_t* num_ranks,
+                                cudaStream_t s);
+cudaError_t launch_fill_rank_matrix(const uint64_t* sorted_keys, const uint32_t* edge_rank, uint32_t num_edges,
+                                    int edge_bits, const CloudInfo* clouds, uint32_t* R, cudaStream_t s);
+cudaError_t launch_neighbor_counts(const uint32_t* R, const CloudInfo* clouds, const uint32_t* vcloud,
+                                   uint32_t nverts, uint32_t* deg, uint32_t* max_deg, cudaStream_t s);
+cudaError_t launch_neighbor_fill(const uint32_t* R, const CloudInfo* clouds, const uint32_t* vcloud, uint32_t nverts,
+                                 const uint32_t* off, uint32_t* nbr, cudaStream_t s);
 cudaError_t launch_distance_matrix(const float* pts, int n, int k, float* D, cudaStream_t s);
+cudaError_t launch_distance_matrices(const float* pts, int k, const CloudInfo* clouds, const uint32_t* tile_off,
+                                     int nclouds, uint32_t tiles, float* D, cudaStream_t s);
 
 // rips_scan.cu: exclusive scan of uint32 (in place allowed); returns total in *d_total if non-null
 size_t scan_temp_bytes(uint32_t n);
@@ -130,73 +152,87 @@ cudaError_t radix_sort_u64(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, u
 
 // One dimension of the reduction (rips_dim.cu)
 struct DimArgs {
-  int n, d;                        // columns are d-simplices
-  const uint32_t* R;               // rank matrix
-  const uint32_t* nbr_off;         // neighbour lists, decreasing order
-  const uint32_t* nbr;
-  const uint64_t* binom;           // global binomial table, stride n+1
+  int d;                           // columns are d-simplices
+  int nclouds;
+  const CloudInfo* clouds;
+  const uint32_t* R;               // rank matrices of all clouds
+  const uint32_t* nbr_off;         // neighbour-list CSR over all clouds' vertices (global rows)
+  const uint32_t* nbr;             // local vertex ids, decreasing within a row
+  const uint64_t* binom;           // binomial table for n_max, stride bn + 1
+  int bn;
   int kmax;                        // rows 0..kmax of the table are staged
   int smem_binom;                  // stage the table in shared memory
   uint32_t p;
-  int row_bits;                    // bits of a (d+1)-simplex index
-  int col_bits;                    // bits of a d-simplex index
+  int row_bits;                    // bits of a local (d+1)-simplex index
+  int col_bits;                    // bits of a local d-simplex index
+  int rank_bits;                   // bits of a diameter rank
   uint32_t rank_max;               // largest diameter rank
   uint32_t* err;
 };
 
-
 // Reduction state (device pointers) shared by the reduction kernels
 struct RedState {
   // columns in processing order
-  const uint64_t* col_keys;   // ((rank_max - rank) << col_bits) | idx
+  const uint64_t* col_keys;   // (cloud << (rank_bits + col_bits)) | ((rank_max - rank) << col_bits) | idx
   uint32_t ncols;
   // per-column state
   uint64_t* piv_key;          // row key of the pivot, IDX_NONE for a zero column
   uint32_t* piv_coef;
-  uint32_t* v_off;            // V_j in the arena (v_len == 0: V_j = e_j)
-  uint32_t* v_len;
   uint8_t* reduced;           // 1 once the column has been added to
-  // V arena
-  uint64_t* v_idx;
-  uint32_t* v_rank;
-  uint32_t* v_coef;
-  unsigned long long* v_top;
-  unsigned long long v_cap;
+  // materialised working columns R_j (sorted row keys, nonzero coefficients)
+  uint64_t* r_key;
+  uint32_t* r_coef;
+  unsigned long long* r_off;  // per column; r_len == 0: not materialised
+  uint32_t* r_len;
+  unsigned long long* r_top;
+  unsigned long long r_cap;
+  // power of two >= 1 + the largest vertex degree: room for one generated coboundary
+  uint32_t scr_slice;
   // pivot table
   uint64_t* t_keys;
   uint32_t* t_vals;
   uint64_t t_mask;
   // work lists
   uint32_t* claim_list;
-  uint32_t* claim_count;
   uint32_t* reduce_list;
-  uint32_t* reduce_count;
   unsigned long long* steps;
+  unsigned long long* compacted;  // entries read by run compactions (profiling)
+  uint32_t* max_chain;            // longest chain of additions (profiling)
   uint32_t* err;
 };
 
 
 // from rips_h0.cu
-cudaError_t run_h0(int n, const uint64_t* sorted_keys, uint32_t m, uint32_t* eu, uint32_t* ev, uint32_t* comp,
-                   uint32_t* best, uint32_t* parent, uint8_t* in_forest, uint32_t* flags, uint32_t* fpos,
-                   void* scan_tmp, uint32_t* d_nf, uint32_t* gtop, rips_bar_t* bars, uint32_t* nbars,
-                   uint32_t bar_cap, int cloud, unsigned long long* stats, uint32_t* err, cudaStream_t s);
+// per-cloud H0 in one block per cloud (every n_c small enough for shared memory)
+bool h0_blocks_fit(int n_max);
+cudaError_t launch_h0_blocks(const CloudInfo* clouds, int nclouds, int n_max, const uint64_t* sorted_keys,
+                             int edge_bits, uint32_t* eu, uint32_t* ev, uint32_t m_total, uint8_t* in_forest,
+                             rips_bar_t* bars, uint32_t* nbars, uint32_t bar_cap, unsigned long long* stats,
+                             int stats_stride, uint32_t* err, cudaStream_t s);
+// one large cloud: Boruvka rounds over the whole GPU, then the elder rule
+cudaError_t run_h0_large(int n, const uint64_t* sorted_keys, uint32_t m, int edge_bits, uint32_t* eu, uint32_t* ev,
+                         uint32_t* comp, uint32_t* best, uint32_t* parent, uint8_t* in_forest, uint32_t* flags,
+                         uint32_t* fpos, void* scan_tmp, uint32_t* d_nf, uint32_t* gtop, rips_bar_t* bars,
+                         uint32_t* nbars, uint32_t bar_cap, unsigned long long* stats, uint32_t* err, cudaStream_t s);
 
 // from rips_dim.cu
 cudaError_t launch_enumerate(const DimArgs& a, const uint64_t* pidx, const uint32_t* prank, uint32_t np,
-                             uint64_t* out_idx, uint32_t* out_rank, unsigned long long* count,
+                             int prev_col_bits, uint64_t* out_idx, uint32_t* out_rank, unsigned long long* count,
                              unsigned long long cap, cudaStream_t st);
-cudaError_t launch_edges_to_simplices(const uint64_t* keys, const uint32_t* erank, uint32_t m, uint64_t* sidx,
-                                      uint32_t* srank, cudaStream_t st);
+cudaError_t launch_edges_to_simplices(const uint64_t* keys, const uint32_t* erank, uint32_t m, int edge_bits,
+                                      int col_bits, uint64_t* sidx, uint32_t* srank, cudaStream_t st);
+// stats: per cloud, stats_stride counters; the test writes [4] cofacet, [5] facet, [6] cleared
 cudaError_t launch_test(const DimArgs& a, const uint64_t* sidx, const uint32_t* srank, uint32_t ns,
                         const uint8_t* cleared_flag, const uint64_t* prev_keys, uint64_t prev_mask,
                         uint64_t* col_keys, uint32_t* ncols, uint32_t col_cap, unsigned long long* stats,
-                        cudaStream_t st);
-cudaError_t launch_init(const DimArgs& a, const RedState& s, cudaStream_t st);
-cudaError_t launch_claim(const DimArgs& a, const RedState& s, uint32_t count, cudaStream_t st);
-cudaError_t launch_reduce(const DimArgs& a, const RedState& s, uint32_t count, cudaStream_t st);
-cudaError_t launch_readout(const DimArgs& a, const RedState& s, const float* rank_value, int cloud,
-                           rips_bar_t* bars, uint32_t* nbars, uint32_t bar_cap, unsigned long long* stats,
+                        int stats_stride, cudaStream_t st);
+// blocks of the cooperative reduction launch (all co-resident), -1 on error
+int reduction_blocks(const DimArgs& a, uint32_t ncols);
+// ctl: 8 zeroed uint32 (see reduce_persistent_kernel); ctl[6] receives the rounds
+cudaError_t launch_reduction(const DimArgs& a, const RedState& s, int blocks, unsigned* ctl, cudaStream_t st);
+// stats: [0] pairs, [1] zero pairs, [2] essential, [3] emergent per cloud
+cudaError_t launch_readout(const DimArgs& a, const RedState& s, const float* rank_value, rips_bar_t* bars,
+                           uint32_t* nbars, uint32_t bar_cap, unsigned long long* stats, int stats_stride,
                            cudaStream_t st);
 
 // from rips_epilogue.cu

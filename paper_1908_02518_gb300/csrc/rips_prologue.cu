@@ -52,14 +52,38 @@ __device__ __forceinline__ void tri_tile(uint32_t b, uint32_t* I, uint32_t* J) {
   *J = b - (uint32_t)((uint64_t)i * (i + 1) / 2);
 }
 
-// Validates the strict lower triangle and accumulates the maximum of every
-// row and column of it (= row maxima of the symmetric matrix) as float bits.
-__global__ void __launch_bounds__(TILE * 8) validate_rowmax_kernel(const float* __restrict__ D, int n,
+// cloud owning block b, given the exclusive prefix off[0..nclouds] of blocks per cloud
+__device__ __forceinline__ int cloud_of_block(const uint32_t* __restrict__ off, int nclouds, uint32_t b) {
+  int lo = 0, hi = nclouds - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void cloud_vertices_kernel(const CloudInfo* __restrict__ clouds, uint32_t* __restrict__ vcloud) {
+  const CloudInfo ci = clouds[blockIdx.x];
+  for (int i = threadIdx.x; i < ci.n; i += blockDim.x) vcloud[ci.voff + i] = blockIdx.x;
+}
+
+// Validates the strict lower triangle of every cloud's matrix and accumulates
+// the maximum of each row and column of it (= row maxima of the symmetric
+// matrix) as float bits.  One block per 32x32 tile of a lower triangle.
+__global__ void __launch_bounds__(TILE * 8) validate_rowmax_kernel(const float* __restrict__ D,
+                                                                   const CloudInfo* __restrict__ clouds,
+                                                                   const uint32_t* __restrict__ tile_off, int nclouds,
                                                                    uint32_t* __restrict__ rowmax,
                                                                    uint32_t* __restrict__ err) {
   __shared__ uint32_t rmax[TILE][TILE + 1];
+  const int c = cloud_of_block(tile_off, nclouds, blockIdx.x);
+  const CloudInfo ci = clouds[c];
+  const int n = ci.n;
+  const float* Dc = D + ci.roff;
+  uint32_t* rm = rowmax + ci.voff;
   uint32_t I, J;
-  tri_tile(blockIdx.x, &I, &J);
+  tri_tile(blockIdx.x - tile_off[c], &I, &J);
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int j = J * TILE + tx;
   bool bad = false;
@@ -68,7 +92,7 @@ __global__ void __launch_bounds__(TILE * 8) validate_rowmax_kernel(const float* 
     const int i = I * TILE + r;
     uint32_t bits = 0;
     if (i < n && j < i) {
-      float v = D[(size_t)i * n + j];
+      float v = Dc[(size_t)i * n + j];
       if (!(v >= 0.0f) || isinf(v)) bad = true;
       else bits = __float_as_uint(v == 0.0f ? 0.0f : v);
     }
@@ -77,13 +101,12 @@ __global__ void __launch_bounds__(TILE * 8) validate_rowmax_kernel(const float* 
   }
   if (bad) set_error(err, ERRF_BAD_INPUT);
   __syncthreads();
-  // row maxima: warp ty reduces rows ty, ty+8, ...
   for (int r = ty; r < TILE; r += 8) {
     uint32_t v = rmax[r][tx];
 #pragma unroll
     for (int o = 16; o; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
     const int i = I * TILE + r;
-    if (tx == 0 && i < n && v) atomicMax(&rowmax[i], v);
+    if (tx == 0 && i < n && v) atomicMax(&rm[i], v);
   }
   __syncthreads();
   rmax[ty][tx] = colmax;
@@ -91,15 +114,17 @@ __global__ void __launch_bounds__(TILE * 8) validate_rowmax_kernel(const float* 
   if (ty == 0) {
     uint32_t v = 0;
     for (int r = 0; r < 8; ++r) v = max(v, rmax[r][tx]);
-    if (j < n && v) atomicMax(&rowmax[j], v);
+    if (j < n && v) atomicMax(&rm[j], v);
   }
 }
 
-__global__ void threshold_kernel(const uint32_t* __restrict__ rowmax, int n, float threshold,
-                                 float* __restrict__ t_eff) {
+// per cloud (one block each): t = threshold, or the enclosing radius
+// min_x max_y d(x, y) when the threshold is +inf or NaN
+__global__ void threshold_kernel(const uint32_t* __restrict__ rowmax, CloudInfo* __restrict__ clouds, float threshold) {
   __shared__ uint32_t sm[32];
+  const CloudInfo ci = clouds[blockIdx.x];
   uint32_t m = 0xFFFFFFFFu;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) m = min(m, rowmax[i]);
+  for (int i = threadIdx.x; i < ci.n; i += blockDim.x) m = min(m, rowmax[ci.voff + i]);
 #pragma unroll
   for (int o = 16; o; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
@@ -107,105 +132,134 @@ __global__ void threshold_kernel(const uint32_t* __restrict__ rowmax, int n, flo
   if (threadIdx.x == 0) {
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = min(m, sm[w]);
     m = min(m, sm[0]);
-    float r = n <= 1 ? 0.0f : __uint_as_float(m);
-    *t_eff = (isnan(threshold) || isinf(threshold)) ? r : threshold;
+    float r = ci.n <= 1 ? 0.0f : __uint_as_float(m);
+    clouds[blockIdx.x].t_eff = (isnan(threshold) || isinf(threshold)) ? r : threshold;
   }
 }
 
-// Edges (i > j) with d(i,j) <= t as keys (float bits << 32) | ~idx, idx = C(i,2)+j.
-__global__ void edge_keys_kernel(const float* __restrict__ D, int n, const float* __restrict__ t_eff,
-                                 uint64_t* __restrict__ keys, uint32_t* __restrict__ count, uint32_t cap) {
-  const float t = *t_eff;
+// Edges (i > j) with d(i,j) <= t as keys
+//   (cloud << (32 + eb)) | (float bits << eb) | (2^eb - 1 - idx),  idx = C(i,2) + j:
+// ascending keys list every cloud's edges contiguously, each cloud in refined
+// filtration order (diameter up, then index down).
+__global__ void edge_keys_kernel(const float* __restrict__ D, const CloudInfo* __restrict__ clouds,
+                                 const uint32_t* __restrict__ vcloud, uint32_t nverts, int eb,
+                                 uint64_t* __restrict__ keys, uint32_t* __restrict__ count,
+                                 uint32_t* __restrict__ cloud_count, uint32_t cap) {
   const int lane = threadIdx.x & 31;
-  const int warps = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
   const unsigned lt = (1u << lane) - 1u;
-  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
+  const uint64_t emask = (1ull << eb) - 1;
+  for (uint32_t v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < nverts; v += warps) {
+    const uint32_t c = vcloud[v];
+    const CloudInfo ci = clouds[c];
+    const int i = (int)(v - ci.voff), n = ci.n;
+    const float t = ci.t_eff;
+    const float* row = D + ci.roff + (size_t)i * n;
     const uint64_t rowbase = (uint64_t)i * (i - 1) / 2;
+    const uint64_t chi = (uint64_t)c << (32 + eb);
     for (int j0 = 0; j0 < i; j0 += 32) {
       const int j = j0 + lane;
-      float v = 0.0f;
+      float x = 0.0f;
       bool ok = false;
       if (j < i) {
-        v = D[(size_t)i * n + j];
-        v = v == 0.0f ? 0.0f : v;
-        ok = v <= t;
+        x = row[j];
+        x = x == 0.0f ? 0.0f : x;
+        ok = x <= t;
       }
       unsigned m = __ballot_sync(0xffffffffu, ok);
       if (!m) continue;
       uint32_t base = 0;
-      if (lane == 0) base = atomicAdd(count, (uint32_t)__popc(m));
+      if (lane == 0) {
+        base = atomicAdd(count, (uint32_t)__popc(m));
+        atomicAdd(&cloud_count[c], (uint32_t)__popc(m));
+      }
       base = __shfl_sync(0xffffffffu, base, 0);
       if (ok) {
         uint32_t pos = base + __popc(m & lt);
-        if (pos < cap)
-          keys[pos] = ((uint64_t)__float_as_uint(v) << 32) | (uint64_t)(0xFFFFFFFFu - (uint32_t)(rowbase + j));
+        if (pos < cap) keys[pos] = chi | ((uint64_t)__float_as_uint(x) << eb) | (emask - (rowbase + j));
       }
     }
   }
 }
 
-__global__ void rank_flags_kernel(const uint64_t* __restrict__ keys, uint32_t m, uint32_t* __restrict__ flags) {
+__global__ void rank_flags_kernel(const uint64_t* __restrict__ keys, uint32_t m, int eb, uint32_t* __restrict__ flags) {
   uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= m) return;
-  flags[e] = (e == 0 || (keys[e] >> 32) != (keys[e - 1] >> 32)) ? 1u : 0u;
+  flags[e] = (e == 0 || (keys[e] >> eb) != (keys[e - 1] >> eb)) ? 1u : 0u;
 }
 
-__global__ void rank_finalize_kernel(const uint64_t* __restrict__ keys, uint32_t m,
+// rank = index of the run of equal (cloud, length) pairs: increasing with the
+// length inside a cloud, so comparing ranks compares lengths exactly
+__global__ void rank_finalize_kernel(const uint64_t* __restrict__ keys, uint32_t m, int eb,
                                      const uint32_t* __restrict__ excl, uint32_t* __restrict__ edge_rank,
                                      float* __restrict__ rank_value) {
   uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= m) return;
-  bool first = (e == 0 || (keys[e] >> 32) != (keys[e - 1] >> 32));
+  bool first = (e == 0 || (keys[e] >> eb) != (keys[e - 1] >> eb));
   uint32_t r = excl[e] + (first ? 1u : 0u) - 1u;
   edge_rank[e] = r;
-  if (first) rank_value[r] = __uint_as_float((uint32_t)(keys[e] >> 32));
+  if (first) rank_value[r] = __uint_as_float((uint32_t)(keys[e] >> eb));
 }
 
-__device__ __forceinline__ void edge_vertices(uint32_t idx, int* a, int* b) {
+__device__ __forceinline__ void edge_vertices(uint64_t idx, int* a, int* b) {
   // largest a with a(a-1)/2 <= idx
   int x = (int)((1.0 + sqrt(1.0 + 8.0 * (double)idx)) * 0.5);
   while ((uint64_t)x * (x - 1) / 2 > idx) --x;
   while ((uint64_t)(x + 1) * x / 2 <= idx) ++x;
   *a = x;
-  *b = (int)(idx - (uint32_t)((uint64_t)x * (x - 1) / 2));
+  *b = (int)(idx - (uint64_t)x * (x - 1) / 2);
 }
 
 __global__ void fill_rank_matrix_kernel(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ edge_rank,
-                                        uint32_t m, int n, uint32_t* __restrict__ R) {
+                                        uint32_t m, int eb, const CloudInfo* __restrict__ clouds,
+                                        uint32_t* __restrict__ R) {
   uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= m) return;
-  uint32_t idx = 0xFFFFFFFFu - (uint32_t)(keys[e] & 0xFFFFFFFFull);
+  const uint64_t key = keys[e];
+  const uint64_t emask = (1ull << eb) - 1;
+  const uint32_t c = (uint32_t)(key >> (32 + eb));
+  const uint64_t idx = emask - (key & emask);
+  const CloudInfo ci = clouds[c];
   int a, b;
   edge_vertices(idx, &a, &b);
-  uint32_t r = edge_rank[e];
-  R[(size_t)a * n + b] = r;
-  R[(size_t)b * n + a] = r;
+  const uint32_t r = edge_rank[e];
+  uint32_t* Rc = R + ci.roff;
+  Rc[(size_t)a * ci.n + b] = r;
+  Rc[(size_t)b * ci.n + a] = r;
 }
 
-// degree of every vertex: number of u with R[v][u] != INF
-__global__ void neighbor_count_kernel(const uint32_t* __restrict__ R, int n, uint32_t* __restrict__ deg) {
+// degree of every vertex: number of u with R[v][u] != INF (one warp per vertex)
+__global__ void neighbor_count_kernel(const uint32_t* __restrict__ R, const CloudInfo* __restrict__ clouds,
+                                      const uint32_t* __restrict__ vcloud, uint32_t nverts,
+                                      uint32_t* __restrict__ deg, uint32_t* __restrict__ max_deg) {
   const int lane = threadIdx.x & 31;
-  const int warps = (gridDim.x * blockDim.x) >> 5;
-  for (int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < nverts; v += warps) {
+    const CloudInfo ci = clouds[vcloud[v]];
+    const uint32_t* row = R + ci.roff + (size_t)(v - ci.voff) * ci.n;
     uint32_t c = 0;
-    const uint32_t* row = R + (size_t)v * n;
-    for (int u = lane; u < n; u += 32) c += row[u] != RANK_INF;
+    for (int u = lane; u < ci.n; u += 32) c += row[u] != RANK_INF;
 #pragma unroll
     for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if (lane == 0) deg[v] = c;
+    if (lane == 0) {
+      deg[v] = c;
+      atomicMax(max_deg, c);
+    }
   }
 }
 
-// neighbour lists in decreasing vertex order
-__global__ void neighbor_fill_kernel(const uint32_t* __restrict__ R, int n, const uint32_t* __restrict__ off,
-                                     uint32_t* __restrict__ nbr) {
+// neighbour lists (local vertex ids) in decreasing order
+__global__ void neighbor_fill_kernel(const uint32_t* __restrict__ R, const CloudInfo* __restrict__ clouds,
+                                     const uint32_t* __restrict__ vcloud, uint32_t nverts,
+                                     const uint32_t* __restrict__ off, uint32_t* __restrict__ nbr) {
   const int lane = threadIdx.x & 31;
-  const int warps = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
   const unsigned lt = (1u << lane) - 1u;
-  for (int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
-    const uint32_t* row = R + (size_t)v * n;
+  for (uint32_t v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < nverts; v += warps) {
+    const CloudInfo ci = clouds[vcloud[v]];
+    const uint32_t* row = R + ci.roff + (size_t)(v - ci.voff) * ci.n;
     uint32_t pos = off[v];
-    for (int u0 = n - 1; u0 >= 0; u0 -= 32) {
+    for (int u0 = ci.n - 1; u0 >= 0; u0 -= 32) {
       int u = u0 - lane;
       bool ok = u >= 0 && row[u] != RANK_INF;
       unsigned m = __ballot_sync(0xffffffffu, ok);
@@ -229,6 +283,26 @@ __global__ void distance_kernel(const float* __restrict__ pts, int n, int k, flo
   D[(size_t)i * n + j] = __double2float_rn(__dsqrt_rn(acc));
 }
 
+// all clouds: one block per 8 rows of a cloud (prefix tile_off over clouds)
+__global__ void distance_multi_kernel(const float* __restrict__ pts, int k, const CloudInfo* __restrict__ clouds,
+                                      const uint32_t* __restrict__ tile_off, int nclouds, float* __restrict__ D) {
+  const int c = cloud_of_block(tile_off, nclouds, blockIdx.x);
+  const CloudInfo ci = clouds[c];
+  const int n = ci.n;
+  const int i = (blockIdx.x - tile_off[c]) * 8 + threadIdx.y;
+  if (i >= n) return;
+  const float* x = pts + (size_t)ci.voff * k;
+  float* Dc = D + ci.roff;
+  for (int j = threadIdx.x; j < n; j += 32) {
+    double acc = 0.0;
+    for (int q = 0; q < k; ++q) {
+      double diff = __dsub_rn((double)x[(size_t)i * k + q], (double)x[(size_t)j * k + q]);
+      acc = __dadd_rn(acc, __dmul_rn(diff, diff));
+    }
+    Dc[(size_t)i * n + j] = __double2float_rn(__dsqrt_rn(acc));
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_binomial_table(uint64_t* tab, int n, int kmax, cudaStream_t s) {
@@ -237,64 +311,82 @@ cudaError_t launch_binomial_table(uint64_t* tab, int n, int kmax, cudaStream_t s
   return cudaGetLastError();
 }
 
-cudaError_t launch_validate_rowmax(const float* D, int n, uint32_t* rowmax_bits, uint32_t* err, cudaStream_t s) {
-  uint32_t nb = (uint32_t)((n + TILE - 1) / TILE);
-  uint32_t blocks = nb * (nb + 1) / 2;
-  validate_rowmax_kernel<<<blocks, TILE * 8, 0, s>>>(D, n, rowmax_bits, err);
+cudaError_t launch_cloud_vertices(const CloudInfo* clouds, int nclouds, uint32_t* vcloud, cudaStream_t s) {
+  cloud_vertices_kernel<<<nclouds, 256, 0, s>>>(clouds, vcloud);
   note_launch();
   return cudaGetLastError();
 }
 
-cudaError_t launch_threshold(const uint32_t* rowmax_bits, int n, float threshold, float* t_eff, cudaStream_t s) {
-  threshold_kernel<<<1, 1024, 0, s>>>(rowmax_bits, n, threshold, t_eff);
+cudaError_t launch_validate_rowmax(const float* D, const CloudInfo* clouds, const uint32_t* tile_off, int nclouds,
+                                   uint32_t tiles, uint32_t* rowmax_bits, uint32_t* err, cudaStream_t s) {
+  if (tiles == 0) return cudaSuccess;
+  validate_rowmax_kernel<<<tiles, TILE * 8, 0, s>>>(D, clouds, tile_off, nclouds, rowmax_bits, err);
   note_launch();
   return cudaGetLastError();
 }
 
-cudaError_t launch_edge_keys(const float* D, int n, const float* t_eff, uint64_t* keys, uint32_t* count,
-                             uint32_t cap, cudaStream_t s) {
-  int blocks = (n * 32 + 255) / 256;
+cudaError_t launch_threshold(const uint32_t* rowmax_bits, CloudInfo* clouds, int nclouds, float threshold,
+                             cudaStream_t s) {
+  threshold_kernel<<<nclouds, 1024, 0, s>>>(rowmax_bits, clouds, threshold);
+  note_launch();
+  return cudaGetLastError();
+}
+
+static int warp_grid(uint64_t items) {
+  uint64_t blocks = (items * 32 + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
-  edge_keys_kernel<<<blocks, 256, 0, s>>>(D, n, t_eff, keys, count, cap);
+  return (int)blocks;
+}
+
+cudaError_t launch_edge_keys(const float* D, const CloudInfo* clouds, const uint32_t* vcloud, uint32_t nverts,
+                             int edge_bits, uint64_t* keys, uint32_t* count, uint32_t* cloud_count, uint32_t cap,
+                             cudaStream_t s) {
+  edge_keys_kernel<<<warp_grid(nverts), 256, 0, s>>>(D, clouds, vcloud, nverts, edge_bits, keys, count, cloud_count,
+                                                    cap);
   note_launch();
   return cudaGetLastError();
 }
 
-cudaError_t launch_assign_ranks(const uint64_t* sorted_keys, uint32_t m, uint32_t* flags, uint32_t* scan_tmp,
-                                size_t, uint32_t* edge_rank, float* rank_value, uint32_t* num_ranks,
+cudaError_t launch_assign_ranks(const uint64_t* sorted_keys, uint32_t m, int edge_bits, uint32_t* flags,
+                                uint32_t* scan_tmp, uint32_t* edge_rank, float* rank_value, uint32_t* num_ranks,
                                 cudaStream_t s) {
   if (m == 0) return cudaMemsetAsync(num_ranks, 0, sizeof(uint32_t), s);
-  rank_flags_kernel<<<(m + 255) / 256, 256, 0, s>>>(sorted_keys, m, flags);
+  rank_flags_kernel<<<(m + 255) / 256, 256, 0, s>>>(sorted_keys, m, edge_bits, flags);
   note_launch();
   cudaError_t e = launch_exclusive_scan(flags, flags, m, scan_tmp, num_ranks, s);
   if (e != cudaSuccess) return e;
-  rank_finalize_kernel<<<(m + 255) / 256, 256, 0, s>>>(sorted_keys, m, flags, edge_rank, rank_value);
+  rank_finalize_kernel<<<(m + 255) / 256, 256, 0, s>>>(sorted_keys, m, edge_bits, flags, edge_rank, rank_value);
   note_launch();
   return cudaGetLastError();
 }
 
-cudaError_t launch_fill_rank_matrix(const uint64_t* sorted_keys, const uint32_t* edge_rank, uint32_t m, int n,
-                                    uint32_t* R, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(R, 0xFF, (size_t)n * n * sizeof(uint32_t), s);
-  if (e != cudaSuccess || m == 0) return e;
-  fill_rank_matrix_kernel<<<(m + 255) / 256, 256, 0, s>>>(sorted_keys, edge_rank, m, n, R);
+cudaError_t launch_fill_rank_matrix(const uint64_t* sorted_keys, const uint32_t* edge_rank, uint32_t m,
+                                    int edge_bits, const CloudInfo* clouds, uint32_t* R, cudaStream_t s) {
+  if (m == 0) return cudaSuccess;
+  fill_rank_matrix_kernel<<<(m + 255) / 256, 256, 0, s>>>(sorted_keys, edge_rank, m, edge_bits, clouds, R);
   note_launch();
   return cudaGetLastError();
 }
 
-cudaError_t launch_neighbor_counts(const uint32_t* R, int n, uint32_t* deg, cudaStream_t s) {
-  int blocks = (n * 32 + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  neighbor_count_kernel<<<blocks, 256, 0, s>>>(R, n, deg);
+cudaError_t launch_neighbor_counts(const uint32_t* R, const CloudInfo* clouds, const uint32_t* vcloud,
+                                   uint32_t nverts, uint32_t* deg, uint32_t* max_deg, cudaStream_t s) {
+  neighbor_count_kernel<<<warp_grid(nverts), 256, 0, s>>>(R, clouds, vcloud, nverts, deg, max_deg);
   note_launch();
   return cudaGetLastError();
 }
 
-cudaError_t launch_neighbor_fill(const uint32_t* R, int n, const uint32_t* off, uint32_t* nbr, cudaStream_t s) {
-  int blocks = (n * 32 + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  neighbor_fill_kernel<<<blocks, 256, 0, s>>>(R, n, off, nbr);
+cudaError_t launch_neighbor_fill(const uint32_t* R, const CloudInfo* clouds, const uint32_t* vcloud, uint32_t nverts,
+                                 const uint32_t* off, uint32_t* nbr, cudaStream_t s) {
+  neighbor_fill_kernel<<<warp_grid(nverts), 256, 0, s>>>(R, clouds, vcloud, nverts, off, nbr);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_distance_matrices(const float* pts, int k, const CloudInfo* clouds, const uint32_t* tile_off,
+                                     int nclouds, uint32_t tiles, float* D, cudaStream_t s) {
+  if (tiles == 0) return cudaSuccess;
+  distance_multi_kernel<<<tiles, dim3(32, 8), 0, s>>>(pts, k, clouds, tile_off, nclouds, D);
   note_launch();
   return cudaGetLastError();
 }

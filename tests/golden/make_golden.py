@@ -3,7 +3,8 @@ oracle only (oracle/, cohomology method).  Run from the repository root:
 
     python tests/golden/make_golden.py [workload ...]
 
-Each workload gives tests/golden/<name>.bars.txt.gz: a header with the SHA-256 of
+Each workload gives tests/golden/<name>.bars.txt.gz (the batched workload:
+batch256.bars.txt.gz, one header per cloud): a header with the SHA-256 of
 the FP32 distance matrix (so a test can check that its input is bit-identical)
 and one line per bar: dim birth_bits death_bits birth_simplex death_simplex
 (float bits in hex, death_simplex -1 for essential classes), plus the oracle's
@@ -58,16 +59,61 @@ def read(path):
     return head, bars
 
 
+def bar_line(dim, birth, death, bs, ds):
+    return (f"{int(dim)} {np.float32(birth).view(np.uint32):08x} {np.float32(death).view(np.uint32):08x} "
+            f"{int(bs)} {int(ds)}")
+
+
+def canonical_digest(bars):
+    """SHA-256 of the bars (dim, birth, death, birth_simplex, death_simplex; -1 for
+    an essential death simplex) sorted as tuples, one bar_line per bar."""
+    import hashlib
+    h = hashlib.sha256()
+    for t in sorted(bars):
+        h.update((bar_line(*t) + "\n").encode())
+    return h.hexdigest()
+
+
 def batch():
+    """All 256 clouds of the batched workload in one file: per cloud a header line
+    ('#' + JSON with its matrix digest, the H0 bar count and the digest of its H0
+    bars) followed by its H1 bars in full."""
     clouds = W.batch_clouds()
-    for c, pts in enumerate(clouds):
-        write(f"batch/cloud{c:03d}", W.distance_matrix(pts), 1, float("inf"), 2, {"cloud": c})
+    path = os.path.join(HERE, "batch256.bars.txt.gz")
+    t0 = time.time()
+    with gzip.open(path, "wt") as f:
+        for c, pts in enumerate(clouds):
+            d = W.distance_matrix(pts)
+            r = oracle.barcodes(d, 1, float("inf"), 2, method="coh")
+            tup = [(int(b["dim"]), float(b["birth"]), float(b["death"]), int(b["birth_simplex"]),
+                    int(b["death_simplex"])) for b in r.bars]
+            h0 = [t for t in tup if t[0] == 0]
+            head = {"cloud": c, "sha256": W.matrix_digest(d), "n": int(d.shape[0]), "threshold_used": r.threshold,
+                    "stats": r.stats, "h0_count": len(h0), "h0_digest": canonical_digest(h0)}
+            f.write("# " + json.dumps(head) + "\n")
+            for t in tup:
+                if t[0] == 1:
+                    f.write(bar_line(*t) + "\n")
+    print(f"batch: {len(clouds)} clouds, oracle {time.time() - t0:.1f} s -> {path}")
+
+
+def read_batch(path):
+    """list of (header, H1 bars) per cloud"""
+    out = []
+    with gzip.open(path, "rt") as f:
+        for line in f:
+            if line.startswith("# "):
+                out.append((json.loads(line[2:]), []))
+                continue
+            d, b, e, bs, ds = line.split()
+            out[-1][1].append((int(d), float(np.uint32(int(b, 16)).view(np.float32)),
+                               float(np.uint32(int(e, 16)).view(np.float32)), int(bs), int(ds)))
+    return out
 
 
 def main(names):
     for name in names:
         if name == "batch":
-            os.makedirs(os.path.join(HERE, "batch"), exist_ok=True)
             batch()
             continue
         w = W.WORKLOADS[name]()

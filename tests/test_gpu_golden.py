@@ -1,0 +1,89 @@
+"""Full-size parity: the CUDA path against the oracle's stored barcodes of the
+five workloads (tests/golden/*.bars.txt.gz, written by
+tests/golden/make_golden.py from oracle/ only).  The input matrix's SHA-256 is
+checked first, so a difference cannot come from the input generator."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_1908_02518_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+U64MAX = int(np.iinfo(np.uint64).max)
+
+
+def _mg():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("make_golden", os.path.join(GOLD, "make_golden.py"))
+    mg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mg)
+    return mg
+
+
+def _read(name):
+    path = os.path.join(GOLD, f"{name}.bars.txt.gz")
+    if not os.path.exists(path):
+        pytest.skip(f"golden file {name} not generated")
+    return _mg().read(path)
+
+
+def _key_gpu(bars):
+    return sorted((int(b["dim"]), float(b["birth"]), float(b["death"]), int(b["birth_simplex"]),
+                   int(b["death_simplex"])) for b in bars)
+
+
+def _key_gold(bars):
+    return sorted((d, b, e, bs, U64MAX if ds < 0 else ds) for d, b, e, bs, ds in bars)
+
+
+HEAVY = {"s3_192", "so3_4096"}
+
+
+@pytest.mark.parametrize("name", ["cube100", "torus1000", "s3_192", "so3_4096"])
+def test_workload_matches_golden(name):
+    import os as _os
+    import torch
+    import paper_1908_02518_gb300 as rg
+    if name in HEAVY and _os.environ.get("RIPS_HEAVY_GOLDEN") != "1":
+        pytest.skip("long single-column reduction chains: run with RIPS_HEAVY_GOLDEN=1")
+    head, bars = _read(name)
+    w = W.WORKLOADS[name]()
+    assert W.matrix_digest(w.dist) == head["sha256"], "input generator is not bit-identical on this host"
+    res = rg.barcodes(torch.from_numpy(w.dist).cuda(), w.dim_max, w.threshold, w.p)
+    assert res.threshold == head["threshold_used"]
+    g, want = _key_gpu(res.bars), _key_gold(bars)
+    if g != want:
+        gs, ws = set(g), set(want)
+        raise AssertionError(f"{len(g)} vs {len(want)}; only gpu {sorted(gs - ws)[:5]}; only oracle {sorted(ws - gs)[:5]}")
+    for d in range(w.dim_max + 1):
+        s, o = res.stats[0][d], head["stats"][d]
+        assert s["simplices"] == o["simplices"]
+        assert s["essential"] == o["essential"]
+        if d:
+            assert s["pairs"] + s["apparent_cofacet"] == o["pairs"]
+
+
+def test_batch_matches_golden():
+    import torch
+    import paper_1908_02518_gb300 as rg
+    clouds = W.batch_clouds()
+    off = np.concatenate([[0], np.cumsum([c.shape[0] for c in clouds])])
+    x = torch.from_numpy(np.concatenate(clouds)).cuda()
+    res = rg.barcodes_batched(x, off, dim_max=1)
+    path = os.path.join(GOLD, "batch256.bars.txt.gz")
+    if not os.path.exists(path):
+        pytest.skip("golden file batch256 not generated")
+    mg = _mg()
+    gold = mg.read_batch(path)
+    assert len(gold) == len(clouds)
+    for c, pts in enumerate(clouds):
+        head, h1 = gold[c]
+        assert W.matrix_digest(W.distance_matrix(pts)) == head["sha256"]
+        assert _key_gpu(res.dim(1, c)) == _key_gold(h1), c
+        h0 = [(d, b, e, bs, -1 if ds == U64MAX else ds) for d, b, e, bs, ds in _key_gpu(res.dim(0, c))]
+        assert len(h0) == head["h0_count"], c
+        assert mg.canonical_digest(h0) == head["h0_digest"], c
