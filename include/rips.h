@@ -143,6 +143,28 @@ RIPS_API int rips_barcodes_backward(const rips_result_t* res, const float* d_poi
                                     const float* grad_birth, const float* grad_death,
                                     float* d_grad_points, float* d_grad_dist, void* cuda_stream);
 
+/*
+ * rips_h0_barcode_noalloc -- the dimension-0 barcode of one distance matrix
+ * without allocating any memory.  No counterpart in the paper: it exists for
+ * callers that cannot allocate device memory while they run (code inside CUDA
+ * graph capture, serving processes whose pool owns the whole device, real-time
+ * loops that must not wait on an allocator).  All intermediate data lives in a
+ * fixed file-scope device array (about 3.3 MB, held by every GPU that loads the
+ * library until the process exits), so n is at most RIPS_NOALLOC_MAX_N; larger
+ * n returns RIPS_ERR_BAD_ARG.  d_dist: n x n FP32 (DEVICE, strict lower
+ * triangle read, as for rips_barcodes); threshold as for rips_barcodes.
+ * d_bars: DEVICE room for n bars, receives the H0 bars (forest edges in
+ * filtration order, then the essential classes); d_nbars: DEVICE uint32, the
+ * bar count.  Work is issued on cuda_stream and the call waits for it.  Every
+ * call reuses the same array and resets what must start at zero: calls that
+ * overlap on the GPU (other streams or threads) race and must not be made.  The
+ * first call on a device looks the array's address up; make it before any
+ * stream capture begins.
+ */
+#define RIPS_NOALLOC_MAX_N 512
+RIPS_API int rips_h0_barcode_noalloc(const float* d_dist, int64_t n, float threshold, rips_bar_t* d_bars,
+                                     uint32_t* d_nbars, void* cuda_stream);
+
 /* Number of bars of cloud `cloud` in dimension `dim` (dim = -1: all dims);
  * cloud = -1: all clouds.  Negative status on a bad argument. */
 RIPS_API int64_t rips_result_num_bars(const rips_result_t* res, int32_t cloud, int32_t dim);

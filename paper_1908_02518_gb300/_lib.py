@@ -35,7 +35,7 @@ EXPORTS = [
     "rips_barcodes_backward", "rips_result_num_bars", "rips_result_bars", "rips_result_num_clouds",
     "rips_result_dim_max", "rips_result_threshold", "rips_result_stats", "rips_result_phase_ms",
     "rips_result_free", "rips_status_string", "rips_kernel_launch_count", "rips_set_kernel_timing",
-    "rips_result_kernel_ms",
+    "rips_result_kernel_ms", "rips_h0_barcode_noalloc",
 ]
 
 KERNEL_CLASSES = ["prologue", "edge_sort", "h0", "enumerate", "apparent", "col_sort", "pivot_init", "reduce",
@@ -92,6 +92,8 @@ def load(build_if_missing: bool = True):
     lib.rips_set_kernel_timing.restype = C.c_int
     lib.rips_result_kernel_ms.argtypes = [vp, i32, fp, C.POINTER(C.c_int64)]
     lib.rips_result_kernel_ms.restype = C.c_int
+    lib.rips_h0_barcode_noalloc.argtypes = [vp, i64, C.c_float, vp, vp, vp]
+    lib.rips_h0_barcode_noalloc.restype = C.c_int
     _lib = lib
     return lib
 
