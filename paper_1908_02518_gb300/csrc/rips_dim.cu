@@ -30,7 +30,11 @@
 //                     going while the new pivot is owned by an earlier column; a
 //                     pivot with a zero apparent facet is owned by that facet's
 //                     column (Section 4, "Persistence pairs": apparent pairs are
-//                     not in the table).
+//                     not in the table).  A warp reduces a column while there
+//                     are more columns than blocks, for at most WARP_CHAIN_LIMIT
+//                     additions a round; with fewer, a block takes each column
+//                     and adds with a block-wide merge, which is what long
+//                     chains of additions need.
 //
 // The coboundary stays implicit (Section 3.4) for every column that is never
 // added to -- apparent, emergent and unreduced owners: their coboundary is
@@ -55,6 +59,7 @@ namespace {
 
 constexpr int WARPS_PER_BLOCK = 8;
 constexpr uint32_t MAX_PIVOT_PASSES = 1u << 18;  // cancellations in a row before giving up
+constexpr uint32_t WARP_CHAIN_LIMIT = 32;         // additions per round of a warp-reduced column
 
 struct Binom {
   const uint64_t* t;
@@ -169,12 +174,14 @@ __device__ __forceinline__ bool cofacet_of(const CV& cv, const Binom& B, const i
                                            const CofacetSums& cs, int j, uint32_t* rank, uint64_t* idx, int* cpos) {
   uint32_t r = srank;
   int c = 0;
-  for (int l = 0; l <= d; ++l) {
-    uint32_t x = cv.R[(size_t)v[l] * cv.n + j];
-    if (x == RANK_INF) return false;
+  bool ok = true;
+  for (int l = 0; l <= d; ++l) {  // no early exit: the loads are independent
+    const uint32_t x = cv.R[(size_t)v[l] * cv.n + j];
+    ok &= x != RANK_INF;
     r = max(r, x);
     c += v[l] > j;
   }
+  if (!ok) return false;
   *rank = r;
   *cpos = c;
   *idx = cs.above[c] + B(j, d + 2 - c) + cs.below[c];
@@ -257,14 +264,9 @@ __device__ int zero_apparent_facet(const CV& cv, const int* w, int k, uint32_t r
       above = u > drop;
       if (above) {
         hit = true;
-        for (int x = 0; x < k; ++x) {
-          uint32_t y = cv.R[(size_t)rv[x] * cv.n + u];
-          if (y > r) {
-            hit = false;
-            break;
-          }
-        }
-        // u must not be a vertex of tau (the dropped vertex is excluded by u > drop)
+        for (int x = 0; x < k; ++x) hit &= cv.R[(size_t)rv[x] * cv.n + u] <= r;
+        // u is not a vertex of tau: the dropped vertex is excluded by u > drop, the
+        // others by R = RANK_INF on the diagonal
       }
     }
     if (__any_sync(0xffffffffu, hit)) return -1;
@@ -651,33 +653,54 @@ __device__ void warp_sort_pairs(uint64_t* key, uint32_t* coef, uint32_t n, int l
 }
 
 // ---------------------------------------------------------------- lazy working column
-// During a chain of additions the working column is a sum of up to 32 sorted
-// runs, one per lane, each with its own Z/p scale: R_j's own entries and the
+// During a chain of additions the working column is a sum of sorted runs, one
+// per lane (at most 32), each with its own Z/p scale: R_j's own entries and the
 // columns added to it.  Adding a column appends a run (no copy of R_j); the
 // pivot is the smallest head key whose combined coefficient is nonzero, found by
-// a warp min-reduction, with the heads at a cancelled key advanced (the paper's
-// lazily evaluated heap, Section 4 "Pivot extraction").  When all 32 lanes hold
-// runs they are merged into one, and at the end of a chain the column is
-// written back as a single run so later columns can add it.
+// warp reductions, and the heads at a key whose coefficients cancel move on:
+// the paper's lazily evaluated working coboundary (Section 4, "Pivot
+// extraction"), with sorted runs in place of its heap.  Runs are merged size-
+// tiered: when four runs fall in the same size class (sizes within a factor of
+// four), they become one, so an entry is merged a logarithmic number of times
+// however long the chain; at the end of a chain the column is merged into one
+// run, which later columns add.
 struct Run {
   const uint64_t* key;
   const uint32_t* coef;
   uint32_t len, cur, scale;
+  uint64_t hk;  // head key, ~0 once the run is used up
+  uint32_t hc;  // head coefficient times scale, mod p
 };
 
-__device__ __forceinline__ uint64_t warp_min_u64(uint64_t x) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    const uint64_t y = __shfl_xor_sync(0xffffffffu, x, o);
-    x = y < x ? y : x;
+__device__ __forceinline__ void run_head(Run& r, uint32_t p) {
+  if (r.cur < r.len) {
+    r.hk = r.key[r.cur];
+    r.hc = (uint32_t)(((uint64_t)r.coef[r.cur] * r.scale) % p);
+  } else {
+    r.hk = ~0ull;
+    r.hc = 0;
   }
-  return x;
 }
 
-__device__ __forceinline__ uint32_t warp_sum_mod(uint32_t x, uint32_t p) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) x = (x + __shfl_xor_sync(0xffffffffu, x, o)) % p;
-  return x;
+__device__ __forceinline__ Run make_run(const uint64_t* k, const uint32_t* c, uint32_t n, uint32_t scale,
+                                        uint32_t p) {
+  Run r{k, c, n, 0, scale, ~0ull, 0};
+  run_head(r, p);
+  return r;
+}
+
+__device__ __forceinline__ Run empty_run() { return Run{nullptr, nullptr, 0, 0, 1, ~0ull, 0}; }
+
+// size class of the run's remaining entries (-1 when used up)
+__device__ __forceinline__ int run_tier(const Run& r) {
+  const uint32_t n = r.len - r.cur;
+  return n ? (31 - __clz(n)) >> 1 : -1;
+}
+
+__device__ __forceinline__ uint64_t warp_min_u64(uint64_t x) {
+  const uint32_t hi = __reduce_min_sync(0xffffffffu, (uint32_t)(x >> 32));
+  const uint32_t lo = __reduce_min_sync(0xffffffffu, (uint32_t)(x >> 32) == hi ? (uint32_t)x : 0xffffffffu);
+  return ((uint64_t)hi << 32) | lo;
 }
 
 // arena allocation by lane 0, broadcast; false when the arena is full
@@ -734,42 +757,74 @@ __device__ bool gen_sorted(const DimArgs& a, const RedState& s, const CV& cv, co
 // coefficient.  Heads at a key whose coefficients cancel are advanced.
 __device__ uint64_t runs_pivot(Run& r, uint32_t p, uint32_t* coef_out) {
   for (;;) {
-    const uint64_t h = r.cur < r.len ? r.key[r.cur] : ~0ull;
-    const uint64_t m = warp_min_u64(h);
+    const uint64_t m = warp_min_u64(r.hk);
     if (m == ~0ull) {
       *coef_out = 0;
       return IDX_NONE;
     }
-    const uint32_t mine = h == m ? (uint32_t)(((uint64_t)r.coef[r.cur] * r.scale) % p) : 0u;
-    const uint32_t c = warp_sum_mod(mine, p);
-    if (c != 0) {
+    const bool at = r.hk == m;
+    const uint32_t c = __reduce_add_sync(0xffffffffu, at ? r.hc : 0u) % p;
+    if (c) {
       *coef_out = c;
       return m;
     }
-    if (h == m) ++r.cur;  // the key cancels: every run holding it moves on
+    if (at) {
+      ++r.cur;
+      run_head(r, p);
+    }
   }
 }
 
-// Merge every run (from its cursor) into one sorted run in the arena; run 0
-// becomes that run and the other lanes are emptied.  False when the arena is full.
-__device__ bool runs_compact(const RedState& s, Run& r, int lane, uint32_t p, unsigned long long* out_off,
-                             uint32_t* out_len) {
-  uint32_t rest = r.len - r.cur;
-#pragma unroll
-  for (int o = 16; o; o >>= 1) rest += __shfl_xor_sync(0xffffffffu, rest, o);
+// move the runs that are not used up to lanes 0 .. nr-1
+__device__ void runs_pack(Run& r, int lane, int* nr) {
+  const unsigned live = __ballot_sync(0xffffffffu, r.hk != ~0ull);
+  const int cnt = __popc(live);
+  const int src = lane < cnt ? (int)__fns(live, 0, lane + 1) : lane;
+  Run t;
+  t.key = (const uint64_t*)__shfl_sync(0xffffffffu, (unsigned long long)r.key, src);
+  t.coef = (const uint32_t*)__shfl_sync(0xffffffffu, (unsigned long long)r.coef, src);
+  t.len = __shfl_sync(0xffffffffu, r.len, src);
+  t.cur = __shfl_sync(0xffffffffu, r.cur, src);
+  t.scale = __shfl_sync(0xffffffffu, r.scale, src);
+  t.hk = __shfl_sync(0xffffffffu, r.hk, src);
+  t.hc = __shfl_sync(0xffffffffu, r.hc, src);
+  r = lane < cnt ? t : empty_run();
+  *nr = cnt;
+}
+
+// Runs to merge now: a size class holding four runs, or every run when all 32
+// lanes are taken; 0 when none.
+__device__ unsigned runs_merge_mask(const Run& r, int lane, int nr) {
+  const int t = lane < nr ? run_tier(r) : -1;
+  const unsigned grp = __match_any_sync(0xffffffffu, t >= 0 ? t : -2 - lane);
+  const unsigned elig = __ballot_sync(0xffffffffu, t >= 0 && __popc(grp) >= 4);
+  if (elig) return __shfl_sync(0xffffffffu, grp, __ffs(elig) - 1);
+  if (nr == 32) return __ballot_sync(0xffffffffu, t >= 0);
+  return 0;
+}
+
+// Merges the runs of the lanes in `mask` (from their cursors) into one run in
+// the arena, scale 1, held by the lowest of those lanes; the others are used
+// up.  One merged entry per step of the warp.  False when the arena is full.
+__device__ bool runs_merge_warp(const RedState& s, Run& r, int lane, uint32_t p, unsigned mask) {
+  const bool in = (mask >> lane) & 1u;
+  const uint32_t rest = __reduce_add_sync(0xffffffffu, in ? r.len - r.cur : 0u);
   unsigned long long off;
   if (!arena_alloc(s, lane, rest ? rest : 1, &off)) return false;
   uint64_t* ok = s.r_key + off;
   uint32_t* oc = s.r_coef + off;
   uint32_t out = 0;
   for (;;) {
-    const uint64_t h = r.cur < r.len ? r.key[r.cur] : ~0ull;
+    const uint64_t h = in ? r.hk : ~0ull;
     const uint64_t m = warp_min_u64(h);
     if (m == ~0ull) break;
-    const uint32_t mine = h == m ? (uint32_t)(((uint64_t)r.coef[r.cur] * r.scale) % p) : 0u;
-    const uint32_t c = warp_sum_mod(mine, p);
-    if (h == m) ++r.cur;
-    if (c != 0) {
+    const bool at = h == m;
+    const uint32_t c = __reduce_add_sync(0xffffffffu, at ? r.hc : 0u) % p;
+    if (at) {
+      ++r.cur;
+      run_head(r, p);
+    }
+    if (c) {
       if (lane == 0) {
         ok[out] = m;
         oc[out] = c;
@@ -779,14 +834,42 @@ __device__ bool runs_compact(const RedState& s, Run& r, int lane, uint32_t p, un
   }
   __syncwarp();
   if (lane == 0) atomicAdd(s.compacted, (unsigned long long)rest);
-  r.key = ok;
-  r.coef = oc;
-  r.len = lane == 0 ? out : 0;
-  r.cur = 0;
-  r.scale = 1;
-  *out_off = off;
-  *out_len = out;
+  if (lane == __ffs(mask) - 1) r = make_run(ok, oc, out, 1, p);
+  else if (in) r = empty_run();
   return true;
+}
+
+// State of column j's chain of additions, held by the warp that runs it.
+struct Chain {
+  Run r;          // this lane's run
+  int nr;         // lanes in use
+  uint32_t step;  // additions so far
+  uint64_t key;   // current pivot, IDX_NONE once the column is zero
+  uint32_t coef;
+  int64_t owner;  // table owner of the pivot, or -1 to look it up
+  bool started;   // R_j's own run is in place
+  uint32_t pcoef; // block mode: pivot coefficient of the column being generated
+};
+
+enum : int { CH_DONE = 0, CH_MERGE = 1, CH_ARENA = 2, CH_LONG = 3, CH_INTERNAL = 4, CH_GEN = 5, CH_GEN_SELF = 6 };
+
+// work handed from warp 0 to its block: runs to merge, or a coboundary to generate
+struct ChainReq {
+  unsigned mask;  // CH_MERGE: lanes of the runs
+  uint64_t gidx;  // CH_GEN, CH_GEN_SELF: the simplex
+  uint32_t grank;
+};
+
+// R_j <- R_j - lambda C, lambda = pivot coefficient ratio (Algorithm 1): the run
+// of C joins the set, then the new pivot is found
+__device__ __forceinline__ void chain_add(const DimArgs& a, Chain& ch, int lane, const uint64_t* wk,
+                                          const uint32_t* wc, uint32_t wn, uint32_t wcoef) {
+  const uint32_t lam = (uint32_t)(((uint64_t)ch.coef * mod_inv(wcoef, a.p)) % a.p);
+  if (lane == ch.nr) ch.r = make_run(wk, wc, wn, (a.p - lam) % a.p, a.p);
+  ++ch.nr;
+  ++ch.step;
+  ch.key = runs_pivot(ch.r, a.p, &ch.coef);
+  ch.owner = -1;
 }
 
 // Column j adds the columns owning its pivot until the pivot is free, owned by
@@ -794,39 +877,69 @@ __device__ bool runs_compact(const RedState& s, Run& r, int lane, uint32_t p, un
 // Sections 3.1 and 3.4).  Owners found in the table are stable while the
 // reduce phase runs (an owner is never on the reduce list), so the chain may
 // take several steps in one round.  A pivot with a zero apparent facet is owned
-// by that facet's column (Section 4, "Persistence pairs").  `owner` is the table
-// owner of the current pivot, or -1 to look it up (apparent facets first).
-// Returns false on arena overflow.
-__device__ bool reduce_chain(const DimArgs& a, const RedState& s, const CV& cv, const Binom& B, int lane,
+// by that facet's column (Section 4, "Persistence pairs").  After `limit`
+// additions the chain stops at the next pivot owned by an earlier column in the
+// table (never at an apparent facet's pivot, which no column may claim); the
+// column then claims that pivot again, loses, and is reduced in a later round.
+// In warp mode (block == false) the warp merges runs and generates coboundaries
+// itself.  In block mode these are handed back to the block: CH_MERGE with the
+// lanes of the runs, CH_GEN with the simplex whose coboundary is to be added
+// (its pivot coefficient in ch.pcoef; chain_add goes on once it is made), and
+// CH_GEN_SELF for R_j's own entries, which block mode sets up first (a column
+// on the reduce list always takes at least one addition).
+__device__ int chain_advance(const DimArgs& a, const RedState& s, const CV& cv, const Binom& B, int lane,
                              const SortTile& tile, uint32_t j, uint64_t jidx, uint32_t jrank, uint32_t cl,
-                             int64_t owner, uint64_t* key, uint32_t* coef) {
-  Run r{nullptr, nullptr, 0, 0, 1};
-  int nr = 0;  // runs in use (lanes 0 .. nr-1)
-  bool changed = false;
-  uint32_t step = 0;
-  for (; *key != IDX_NONE; ++step) {
-    if (step > MAX_PIVOT_PASSES) {
-      set_error(a.err, ERRF_TIMEOUT);
-      return true;
+                             uint32_t limit, bool block, Chain& ch, ChainReq* req) {
+  for (;;) {
+    if (ch.nr == 32) runs_pack(ch.r, lane, &ch.nr);  // every lane taken: drop the used-up runs
+    const unsigned mm = runs_merge_mask(ch.r, lane, ch.nr);
+    if (mm) {
+      if (block) {
+        req->mask = mm;
+        return CH_MERGE;
+      }
+      if (!runs_merge_warp(s, ch.r, lane, a.p, mm)) return CH_ARENA;
+      runs_pack(ch.r, lane, &ch.nr);
+      continue;
+    }
+    if (ch.key == IDX_NONE) return CH_DONE;
+    if (ch.step > MAX_PIVOT_PASSES) return CH_LONG;
+    if (block && !ch.started) {
+      const uint32_t jn = s.r_len[j];
+      if (!jn) {
+        req->gidx = jidx;
+        req->grank = jrank;
+        return CH_GEN_SELF;
+      }
+      if (lane == 0) ch.r = make_run(s.r_key + s.r_off[j], s.r_coef + s.r_off[j], jn, 1, a.p);
+      ch.nr = 1;
+      ch.started = true;
     }
     // the column owning the current pivot: an apparent facet, or the table's owner
     const uint64_t* wk;
     const uint32_t* wc;
     uint32_t wn, wcoef;
-    if (owner < 0) {
+    if (ch.owner < 0) {
       uint32_t frank, tcoef;
-      const uint64_t fidx = pivot_apparent_facet(a, cv, B, lane, *key, &frank, &tcoef);
+      const uint64_t fidx = pivot_apparent_facet(a, cv, B, lane, ch.key, &frank, &tcoef);
       if (fidx == IDX_NONE) {
-        const int64_t slot = table_find(s.t_keys, s.t_mask, table_key(a, cl, row_key_idx(a, *key)));
+        const int64_t slot = table_find(s.t_keys, s.t_mask, table_key(a, cl, row_key_idx(a, ch.key)));
         const uint32_t k = slot >= 0 ? s.t_vals[slot] : 0xFFFFFFFFu;
-        if (k >= j) break;  // free, or owned by a later column: claim it next round
-        owner = k;
+        if (k >= j) return CH_DONE;           // free, or owned by a later column: claim it next round
+        if (ch.step >= limit) return CH_DONE;  // long chain: the next round goes on with it
+        ch.owner = k;
         continue;
       }
-      if (!gen_sorted(a, s, cv, B, lane, tile, fidx, frank, &wk, &wc, &wn)) return false;
+      if (block) {
+        req->gidx = fidx;
+        req->grank = frank;
+        ch.pcoef = tcoef;
+        return CH_GEN;
+      }
+      if (!gen_sorted(a, s, cv, B, lane, tile, fidx, frank, &wk, &wc, &wn)) return CH_ARENA;
       wcoef = tcoef;
     } else {
-      const uint32_t k = (uint32_t)owner;
+      const uint32_t k = (uint32_t)ch.owner;
       wcoef = s.piv_coef[k];
       if (s.r_len[k]) {
         wk = s.r_key + s.r_off[k];
@@ -836,55 +949,83 @@ __device__ bool reduce_chain(const DimArgs& a, const RedState& s, const CV& cv, 
         uint64_t kidx;
         uint32_t kr, kcl;
         column_simplex(a, s, k, &kidx, &kr, &kcl);
-        if (!gen_sorted(a, s, cv, B, lane, tile, kidx, kr, &wk, &wc, &wn)) return false;
+        if (block) {
+          req->gidx = kidx;
+          req->grank = kr;
+          ch.pcoef = wcoef;
+          return CH_GEN;
+        }
+        if (!gen_sorted(a, s, cv, B, lane, tile, kidx, kr, &wk, &wc, &wn)) return CH_ARENA;
       }
     }
     // the working column's own entries, on first use
-    if (nr == 0) {
-      const uint64_t* jk;
-      const uint32_t* jc;
-      uint32_t jn;
-      if (s.r_len[j]) {
+    if (!ch.started) {
+      const uint64_t* jk = nullptr;
+      const uint32_t* jc = nullptr;
+      uint32_t jn = s.r_len[j];
+      if (jn) {
         jk = s.r_key + s.r_off[j];
         jc = s.r_coef + s.r_off[j];
-        jn = s.r_len[j];
       } else if (!gen_sorted(a, s, cv, B, lane, tile, jidx, jrank, &jk, &jc, &jn)) {
-        return false;
+        return CH_ARENA;
       }
-      if (lane == 0) r = Run{jk, jc, jn, 0, 1};
-      nr = 1;
+      if (lane == 0) ch.r = make_run(jk, jc, jn, 1, a.p);
+      ch.nr = 1;
+      ch.started = true;
     }
-    if (nr == 32) {
-      unsigned long long o;
-      uint32_t l;
-      if (!runs_compact(s, r, lane, a.p, &o, &l)) return false;
-      nr = 1;
-    }
-    // R_j <- R_j - lambda R_owner, lambda = pivot coefficient ratio (Algorithm 1)
-    const uint32_t lam = (uint32_t)(((uint64_t)(*coef) * mod_inv(wcoef, a.p)) % a.p);
-    if (lane == nr) r = Run{wk, wc, wn, 0, (a.p - lam) % a.p};
-    ++nr;
-    changed = true;
-    if (lane == 0) {
-      s.reduced[j] = 1;
-      atomicAdd(s.steps, 1ull);
-    }
-    *key = runs_pivot(r, a.p, coef);
-    owner = -1;
+    chain_add(a, ch, lane, wk, wc, wn, wcoef);
   }
-  if (lane == 0 && step) atomicMax(s.max_chain, step);
-  // write the working column back as one run so later columns can add it
-  if (changed && *key != IDX_NONE) {
-    unsigned long long o;
-    uint32_t l;
-    if (!runs_compact(s, r, lane, a.p, &o, &l)) return false;
-    if (lane == 0) {
-      s.r_off[j] = o;
-      s.r_len[j] = l;
+}
+
+// Lanes whose runs must be merged before the column is stored as one run (0:
+// it already is one run of scale 1).
+__device__ __forceinline__ unsigned chain_store_mask(const Chain& ch, int lane) {
+  const unsigned live = __ballot_sync(0xffffffffu, lane < ch.nr && ch.r.hk != ~0ull);
+  const unsigned scaled = __ballot_sync(0xffffffffu, lane < ch.nr && ch.r.hk != ~0ull && ch.r.scale != 1);
+  return (__popc(live) > 1 || scaled) ? live : 0u;
+}
+
+// Results of a finished chain: statistics, R_j (lane 0's run after
+// chain_store_mask came back 0) when the column changed and is not zero, the
+// pivot, and the claim list.
+__device__ void chain_finish(const RedState& s, const Chain& ch, int lane, uint32_t j, uint32_t* claim_count) {
+  Run r = ch.r;
+  const uint32_t src = __ffs(__ballot_sync(0xffffffffu, lane < ch.nr && r.hk != ~0ull)) - 1;
+  const unsigned long long off = __shfl_sync(0xffffffffu, (unsigned long long)(r.key + r.cur), src & 31);
+  const uint32_t len = __shfl_sync(0xffffffffu, r.len - r.cur, src & 31);
+  if (lane != 0) return;
+  if (ch.step) {
+    s.reduced[j] = 1;
+    atomicAdd(s.steps, (unsigned long long)ch.step);
+    atomicMax(s.max_chain, ch.step);
+    if (ch.key != IDX_NONE) {
+      s.r_off[j] = (unsigned long long)((const uint64_t*)off - s.r_key);
+      s.r_len[j] = len;
     }
-    __syncwarp();
   }
-  return true;
+  s.piv_key[j] = ch.key;
+  s.piv_coef[j] = ch.coef;
+  if (ch.key != IDX_NONE) s.claim_list[atomicAdd(claim_count, 1u)] = j;
+}
+
+// warp mode: run the chain to its end and store the column
+__device__ int chain_warp(const DimArgs& a, const RedState& s, const CV& cv, const Binom& B, int lane,
+                          const SortTile& tile, uint32_t j, uint64_t jidx, uint32_t jrank, uint32_t cl, uint32_t limit,
+                          Chain& ch) {
+  int st = chain_advance(a, s, cv, B, lane, tile, j, jidx, jrank, cl, limit, false, ch, nullptr);
+  if (st != CH_DONE) return st;
+  if (ch.step && ch.key != IDX_NONE) {
+    const unsigned m = chain_store_mask(ch, lane);
+    if (m) {
+      if (!runs_merge_warp(s, ch.r, lane, a.p, m)) return CH_ARENA;
+      runs_pack(ch.r, lane, &ch.nr);
+    }
+  }
+  return CH_DONE;
+}
+
+__device__ __forceinline__ void chain_error(const DimArgs& a, int st) {
+  set_error(a.err, st == CH_ARENA ? ERRF_ARENA : st == CH_LONG ? ERRF_TIMEOUT : ERRF_INTERNAL);
 }
 
 // First pivot of column j: the cofacets are scanned in decreasing index order and
@@ -923,15 +1064,13 @@ __device__ void init_column(const DimArgs& a, const RedState& s, const Binom& B,
   }
   __syncwarp();
   // during the first phase the table is empty: only apparent facets can own a pivot
-  if (key != IDX_NONE && !reduce_chain(a, s, cv, B, lane, tile, j, idx, r, cl, -1, &key, &coef)) {
-    set_error(a.err, ERRF_ARENA);  // the host restarts this dimension with a larger arena
-    key = IDX_NONE;
+  Chain ch{empty_run(), 0, 0, key, coef, -1, false, 0};
+  const int st = chain_warp(a, s, cv, B, lane, tile, j, idx, r, cl, ~0u, ch);
+  if (st != CH_DONE) {
+    chain_error(a, st);  // an arena overflow restarts this dimension with a larger arena
+    return;
   }
-  if (lane == 0) {
-    s.piv_key[j] = key;
-    s.piv_coef[j] = coef;
-    if (key != IDX_NONE) s.claim_list[atomicAdd(claim_count, 1u)] = j;
-  }
+  chain_finish(s, ch, lane, j, claim_count);
 }
 
 // Column j claims its pivot: the smallest ordinal owns it; the loser (j, or the
@@ -949,35 +1088,403 @@ __device__ void claim_one(const DimArgs& a, const RedState& s, uint32_t j, uint3
   else if (old != 0xFFFFFFFFu && old != j) s.reduce_list[atomicAdd(reduce_count, 1u)] = old;
 }
 
+// owner of column j's current pivot in the table, which must precede j
+__device__ __forceinline__ int64_t reduce_owner(const DimArgs& a, const RedState& s, uint32_t j, uint32_t cl,
+                                                uint64_t key) {
+  const int64_t slot = table_find(s.t_keys, s.t_mask, table_key(a, cl, row_key_idx(a, key)));
+  const uint32_t k = slot >= 0 ? s.t_vals[slot] : 0xFFFFFFFFu;
+  return k < j ? (int64_t)k : -1;
+}
+
 // Column j (its pivot owned by an earlier column) reduces as far as it can in
-// this round and goes back to the claim list unless it became zero.
+// this round, one warp, at most WARP_CHAIN_LIMIT additions, and goes back to
+// the claim list unless it became zero.
 __device__ void reduce_one(const DimArgs& a, const RedState& s, const Binom& B, int lane, const SortTile& tile,
                            uint32_t j, uint32_t* claim_count) {
   uint64_t jidx;
   uint32_t jr, cl;
   column_simplex(a, s, j, &jidx, &jr, &cl);
   const CV cv = cloud_view(a, cl);
-  uint64_t key = s.piv_key[j];
-  uint32_t coef = s.piv_coef[j];
-  const int64_t slot = table_find(s.t_keys, s.t_mask, table_key(a, cl, row_key_idx(a, key)));
-  if (slot < 0) {
+  Chain ch{empty_run(), 0, 0, s.piv_key[j], s.piv_coef[j], -1, false, 0};
+  ch.owner = reduce_owner(a, s, j, cl, ch.key);
+  if (ch.owner < 0) {
     set_error(a.err, ERRF_INTERNAL);
     return;
   }
-  const uint32_t k = s.t_vals[slot];
-  if (k >= j) {
-    set_error(a.err, ERRF_INTERNAL);
+  const int st = chain_warp(a, s, cv, B, lane, tile, j, jidx, jr, cl, WARP_CHAIN_LIMIT, ch);
+  if (st != CH_DONE) {
+    chain_error(a, st);
     return;
   }
-  if (!reduce_chain(a, s, cv, B, lane, tile, j, jidx, jr, cl, (int64_t)k, &key, &coef)) {
-    set_error(a.err, ERRF_ARENA);
+  chain_finish(s, ch, lane, j, claim_count);
+}
+
+// ---------------------------------------------------------------- block mode
+// When a round has at most one column to reduce per block, each block takes a
+// column: warp 0 runs the chain and the pivot search as in warp mode, and the
+// merges of runs are done by the whole block, two runs at a time, with a
+// block-wide merge of 512 entries per tile.
+
+constexpr uint32_t MERGE_T = 2 * WARPS_PER_BLOCK * 32;  // merged entries per tile, two per thread
+constexpr uint32_t FROM_B = 0x80000000u;                // merged entry taken from the second run
+
+struct MergeSmem {
+  uint64_t a_key[MERGE_T + 1];
+  uint64_t b_key[MERGE_T + 1];
+  uint64_t m_key[MERGE_T];
+  uint32_t a_coef[MERGE_T + 1];  // coefficients times the run's scale, mod p
+  uint32_t b_coef[MERGE_T + 1];
+  uint32_t m_val[MERGE_T];  // coefficient, FROM_B set for entries of the second run
+  uint32_t warp_sum[WARPS_PER_BLOCK];
+  uint32_t split_a, split_b;
+};
+constexpr size_t RED_SMEM_BYTES = (size_t)WARPS_PER_BLOCK * SORT_TILE * 12;  // the warps' sort tiles
+static_assert(sizeof(MergeSmem) <= RED_SMEM_BYTES, "merge tile overlays the sort tiles");
+
+struct RunDesc {
+  const uint64_t* key;
+  const uint32_t* coef;
+  uint32_t len, scale;
+};
+
+// a request from warp 0 to the block (see chain_advance), and the block's scratch
+struct MergeReq {
+  RunDesc d[32];  // runs to merge
+  uint32_t n;
+  unsigned mask;
+  int state;
+  uint64_t gidx;  // simplex whose coboundary is to be generated
+  uint32_t grank;
+  uint32_t wsum[WARPS_PER_BLOCK];
+  unsigned long long off;
+};
+
+constexpr uint32_t GEN_SMEM_CAP = (uint32_t)(RED_SMEM_BYTES / 12);  // generated entries sorted in shared memory
+
+// ascending bitonic sort of n2 (a power of two) (key, coef) pairs by the whole block
+__device__ void block_bitonic(uint64_t* key, uint32_t* coef, uint32_t n2) {
+  for (uint32_t k = 2; k <= n2; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = threadIdx.x; i < n2; i += blockDim.x) {
+        const uint32_t l = i ^ j;
+        if (l > i) {
+          const uint64_t ki = key[i], kl = key[l];
+          if ((ki > kl) == ((i & k) == 0)) {
+            key[i] = kl;
+            key[l] = ki;
+            const uint32_t t = coef[i];
+            coef[i] = coef[l];
+            coef[l] = t;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Coboundary of the d-simplex (idx, rank) generated by the whole block: each
+// thread tests one neighbour of the simplex's vertex with the fewest
+// neighbours, a block scan packs the cofacets, a bitonic network sorts them in
+// shared memory (in an arena buffer when more than GEN_SMEM_CAP are possible),
+// and they are stored in the arena.  *out gets the run (scale 1).  Called by
+// the whole block; false (in every thread) when the arena is full.
+__device__ bool block_gen_sorted(const DimArgs& a, const RedState& s, const CV& cv, const Binom& B,
+                                 unsigned char* raw, MergeReq& q, uint64_t idx, uint32_t rank, RunDesc* out) {
+  const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int d = a.d;
+  int v[MAX_DIM + 2];
+  decode(B, cv.n, idx, d, v);
+  CofacetSums cs;
+  cofacet_sums(B, v, d, cs);
+  const int av = v[min_degree_vertex(cv, v, d + 1)];
+  const uint32_t beg = cv.off[av], end = cv.off[av + 1];
+  uint32_t p2 = 1;
+  while (p2 < end - beg) p2 <<= 1;
+  uint64_t* bk = (uint64_t*)raw;
+  uint32_t* bc = (uint32_t*)(raw + (size_t)GEN_SMEM_CAP * 8);
+  const bool in_arena = p2 > GEN_SMEM_CAP;
+  if (in_arena) {
+    if (tid == 0) q.off = atomicAdd(s.r_top, (unsigned long long)p2);
+    __syncthreads();
+    const unsigned long long off = q.off;
+    if (off + p2 > s.r_cap) return false;
+    bk = s.r_key + off;
+    bc = s.r_coef + off;
+  }
+  uint32_t cnt = 0;
+  for (uint32_t q0 = beg; q0 < end; q0 += blockDim.x) {
+    const uint32_t qq = q0 + tid;
+    uint32_t r = 0;
+    uint64_t tidx = 0;
+    int c = 0;
+    const bool ok = qq < end && cofacet_of(cv, B, v, d, rank, cs, (int)cv.nbr[qq], &r, &tidx, &c);
+    const unsigned m = __ballot_sync(0xffffffffu, ok);
+    if (lane == 0) q.wsum[wid] = __popc(m);
+    __syncthreads();
+    uint32_t base = 0, tot = 0;
+    for (uint32_t w = 0; w < WARPS_PER_BLOCK; ++w) {
+      const uint32_t t = q.wsum[w];
+      if (w < wid) base += t;
+      tot += t;
+    }
+    if (ok) {
+      const uint32_t pos = cnt + base + __popc(m & ((1u << lane) - 1u));
+      bk[pos] = row_key(a, r, tidx);
+      bc[pos] = ((d - c) & 1) ? a.p - 1 : 1u;  // the paper's orientation, as in gen_coboundary
+    }
+    cnt += tot;
+    __syncthreads();  // wsum is reused
+  }
+  uint32_t n2 = 1;
+  while (n2 < cnt) n2 <<= 1;
+  for (uint32_t i = cnt + tid; i < n2; i += blockDim.x) {
+    bk[i] = ~0ull;
+    bc[i] = 0;
+  }
+  __syncthreads();
+  block_bitonic(bk, bc, n2);
+  if (in_arena) {
+    *out = RunDesc{bk, bc, cnt, 1};
+    return true;
+  }
+  if (tid == 0) q.off = atomicAdd(s.r_top, (unsigned long long)(cnt ? cnt : 1));
+  __syncthreads();
+  const unsigned long long off = q.off;
+  if (off + cnt > s.r_cap) return false;
+  for (uint32_t i = tid; i < cnt; i += blockDim.x) {
+    s.r_key[off + i] = bk[i];
+    s.r_coef[off + i] = bc[i];
+  }
+  __syncthreads();
+  *out = RunDesc{s.r_key + off, s.r_coef + off, cnt, 1};
+  return true;
+}
+
+// out = sa * A + sb * B over Z/p, A and B sorted with distinct keys each;
+// entries whose coefficient vanishes are dropped.  Each tile stages the next
+// MERGE_T + 1 entries of both runs in shared memory; thread t finds where
+// merged entries 2t and 2t+1 come from by a merge-path search (equal keys: A
+// first), an A entry followed by a B entry with the same key takes their sum
+// and the B entry is dropped, and a block scan packs the nonzero entries.
+// Called by the whole block; returns the output length, the same in every
+// thread.
+__device__ uint32_t block_axpy(MergeSmem& ms, const RunDesc& A, const RunDesc& Bd, uint32_t p, uint64_t* ok,
+                               uint32_t* oc) {
+  const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const uint32_t na = A.len, nb = Bd.len;
+  uint32_t ia = 0, ib = 0, out = 0;
+  uint64_t prev = ~0ull;  // key of the previous tile's last merged entry
+  while (ia < na || ib < nb) {
+    const uint32_t rest = (na - ia) + (nb - ib);
+    const uint32_t nout = rest < MERGE_T ? rest : MERGE_T;
+    for (uint32_t i = tid; i <= MERGE_T; i += blockDim.x) {
+      const bool ha = i < na - ia, hb = i < nb - ib;
+      ms.a_key[i] = ha ? A.key[ia + i] : ~0ull;
+      ms.a_coef[i] = ha ? (uint32_t)(((uint64_t)A.coef[ia + i] * A.scale) % p) : 0u;
+      ms.b_key[i] = hb ? Bd.key[ib + i] : ~0ull;
+      ms.b_coef[i] = hb ? (uint32_t)(((uint64_t)Bd.coef[ib + i] * Bd.scale) % p) : 0u;
+    }
+    __syncthreads();
+    const uint32_t q0 = 2 * tid < nout ? 2 * tid : nout;
+    const uint32_t q1 = q0 + 2 < nout ? q0 + 2 : nout;
+    // x = number of A entries among the first q0 merged ones
+    uint32_t lo = 0, hi = q0;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (ms.a_key[mid] <= ms.b_key[q0 - 1 - mid]) lo = mid + 1;
+      else hi = mid;
+    }
+    uint32_t x = lo, y = q0 - lo;
+    for (uint32_t q = q0; q < q1; ++q) {
+      const uint64_t ka = ms.a_key[x], kb = ms.b_key[y];
+      if (ka <= kb) {
+        ms.m_key[q] = ka;
+        ms.m_val[q] = ms.a_coef[x++];
+      } else {
+        ms.m_key[q] = kb;
+        ms.m_val[q] = FROM_B | ms.b_coef[y++];
+      }
+    }
+    if (q0 < q1 && q1 == nout) {
+      ms.split_a = x;
+      ms.split_b = y;
+    }
+    __syncthreads();
+    const uint32_t sa = ms.split_a, sb = ms.split_b;
+    // the first entry after this tile, when it comes from B
+    const uint64_t nk = ms.b_key[sb] < ms.a_key[sa] ? ms.b_key[sb] : ~0ull;
+    const uint32_t nv = ms.b_coef[sb];
+    uint64_t kk[2];
+    uint32_t vv[2];
+    uint32_t cnt = 0;
+    for (uint32_t q = q0; q < q1; ++q) {
+      const uint64_t k = ms.m_key[q];
+      const uint32_t v = ms.m_val[q];
+      uint32_t c;
+      if (v & FROM_B) {
+        c = (q ? ms.m_key[q - 1] : prev) == k ? 0u : (v & ~FROM_B);  // already summed into the A entry
+      } else {
+        c = v;
+        if (q + 1 < nout) {
+          if ((ms.m_val[q + 1] & FROM_B) && ms.m_key[q + 1] == k) c = (c + (ms.m_val[q + 1] & ~FROM_B)) % p;
+        } else if (nk == k) {
+          c = (c + nv) % p;
+        }
+      }
+      if (c) {
+        kk[cnt] = k;
+        vv[cnt] = c;
+        ++cnt;
+      }
+    }
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= (uint32_t)o) incl += t;
+    }
+    if (lane == 31) ms.warp_sum[wid] = incl;
+    __syncthreads();
+    uint32_t base = 0, total = 0;
+    for (uint32_t w = 0; w < WARPS_PER_BLOCK; ++w) {
+      const uint32_t t = ms.warp_sum[w];
+      if (w < wid) base += t;
+      total += t;
+    }
+    const uint32_t pos = out + base + incl - cnt;
+    for (uint32_t e = 0; e < cnt; ++e) {
+      ok[pos + e] = kk[e];
+      oc[pos + e] = vv[e];
+    }
+    prev = ms.m_key[nout - 1];
+    ia += sa;
+    ib += sb;
+    out += total;
+    __syncthreads();  // the windows and sums are overwritten by the next tile
+  }
+  return out;
+}
+
+// The runs of a merge request, summed two at a time (a tree of block_axpy)
+// into q.d[0] with scale 1.  Called by the whole block; false (in every
+// thread) when the arena is full.
+__device__ bool block_merge_runs(const RedState& s, MergeSmem& ms, MergeReq& q, uint32_t p) {
+  const RunDesc none{nullptr, nullptr, 0, 1};
+  uint32_t n = q.n;
+  while (n > 1 || (n == 1 && q.d[0].scale != 1)) {
+    const uint32_t h = n > 1 ? n >> 1 : 1;
+    for (uint32_t i = 0; i < h; ++i) {
+      const RunDesc A = q.d[2 * i];
+      const RunDesc Bd = n > 1 ? q.d[2 * i + 1] : none;
+      const unsigned long long want = (unsigned long long)A.len + Bd.len;
+      if (threadIdx.x == 0) q.off = atomicAdd(s.r_top, want ? want : 1ull);
+      __syncthreads();
+      const unsigned long long off = q.off;
+      if (off + want > s.r_cap) return false;
+      const uint32_t len = block_axpy(ms, A, Bd, p, s.r_key + off, s.r_coef + off);
+      if (threadIdx.x == 0) {
+        q.d[i] = RunDesc{s.r_key + off, s.r_coef + off, len, 1};
+        atomicAdd(s.compacted, want);
+      }
+      __syncthreads();
+    }
+    if (n > 1 && (n & 1)) {
+      if (threadIdx.x == 0) q.d[h] = q.d[n - 1];
+      __syncthreads();
+    }
+    n = n > 1 ? h + (n & 1) : 1;
+  }
+  return true;
+}
+
+// Column j of the reduce list, reduced by the whole block (see block mode):
+// warp 0 runs the chain, and the block generates coboundaries and merges runs
+// when warp 0 asks for it.  The chain has no step limit here.
+__device__ void reduce_one_block(const DimArgs& a, const RedState& s, const Binom& B, const SortTile& tile,
+                                 unsigned char* raw, MergeReq& q, uint32_t j, uint32_t* claim_count) {
+  MergeSmem& ms = *(MergeSmem*)raw;
+  const uint32_t tid = threadIdx.x;
+  const int lane = tid & 31;
+  uint64_t jidx;
+  uint32_t jr, cl;
+  column_simplex(a, s, j, &jidx, &jr, &cl);
+  const CV cv = cloud_view(a, cl);
+  Chain ch{empty_run(), 0, 0, 0, 0, -1, false, 0};  // meaningful in warp 0 only
+  bool finishing = false;
+  if (tid < 32) {
+    ch.key = s.piv_key[j];
+    ch.coef = s.piv_coef[j];
+    ch.owner = reduce_owner(a, s, j, cl, ch.key);
+  }
+  int state = CH_DONE;
+  for (;;) {
+    if (tid < 32) {
+      ChainReq cr{0u, 0ull, 0u};
+      int st = CH_DONE;
+      if (ch.owner < 0 && ch.step == 0) st = CH_INTERNAL;
+      else if (!finishing) st = chain_advance(a, s, cv, B, lane, tile, j, jidx, jr, cl, ~0u, true, ch, &cr);
+      if (st == CH_DONE && !finishing) {  // the chain ended: R_j must become one run
+        finishing = true;
+        if (ch.step && ch.key != IDX_NONE) {
+          cr.mask = chain_store_mask(ch, lane);
+          if (cr.mask) st = CH_MERGE;
+        }
+      }
+      if (st == CH_MERGE) {
+        const unsigned mask = cr.mask;
+        if ((mask >> lane) & 1u)
+          q.d[__popc(mask & ((1u << lane) - 1u))] =
+              RunDesc{ch.r.key + ch.r.cur, ch.r.coef + ch.r.cur, ch.r.len - ch.r.cur, ch.r.scale};
+        if (lane == 0) {
+          q.n = __popc(mask);
+          q.mask = mask;
+        }
+      }
+      if (lane == 0) {
+        q.state = st;
+        q.gidx = cr.gidx;
+        q.grank = cr.grank;
+      }
+    }
+    __syncthreads();
+    state = q.state;
+    if (state == CH_MERGE) {
+      if (!block_merge_runs(s, ms, q, a.p)) {
+        state = CH_ARENA;
+        break;
+      }
+      if (tid < 32) {  // the merged run replaces the runs it was made of
+        const unsigned mask = q.mask;
+        if (lane == __ffs(mask) - 1) ch.r = make_run(q.d[0].key, q.d[0].coef, q.d[0].len, 1, a.p);
+        else if ((mask >> lane) & 1u) ch.r = empty_run();
+        runs_pack(ch.r, lane, &ch.nr);
+      }
+    } else if (state == CH_GEN || state == CH_GEN_SELF) {
+      RunDesc g;
+      if (!block_gen_sorted(a, s, cv, B, raw, q, q.gidx, q.grank, &g)) {
+        state = CH_ARENA;
+        break;
+      }
+      if (tid < 32) {
+        if (state == CH_GEN_SELF) {
+          if (lane == 0) ch.r = make_run(g.key, g.coef, g.len, 1, a.p);
+          ch.nr = 1;
+          ch.started = true;
+        } else {
+          chain_add(a, ch, lane, g.key, g.coef, g.len, ch.pcoef);
+        }
+      }
+    } else {
+      break;
+    }
+  }
+  if (tid >= 32) return;
+  if (state != CH_DONE) {
+    if (lane == 0) chain_error(a, state);
     return;
   }
-  if (lane == 0) {
-    s.piv_key[j] = key;
-    s.piv_coef[j] = coef;
-    if (key != IDX_NONE) s.claim_list[atomicAdd(claim_count, 1u)] = j;
-  }
+  chain_finish(s, ch, lane, j, claim_count);
 }
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -1026,7 +1533,7 @@ __device__ bool grid_barrier(unsigned* count, unsigned* gen, uint32_t* err) {
 // barriers, until no column is left to claim.  Work-list counters are double
 // buffered by round parity (ctl[0..1] claim, ctl[2..3] reduce); ctl[4..5] are
 // the barrier's counter and generation, ctl[6] receives the number of rounds.
-__global__ void __launch_bounds__(256) reduce_persistent_kernel(DimArgs a, RedState s, unsigned* ctl) {
+__global__ void __launch_bounds__(256, 3) reduce_persistent_kernel(DimArgs a, RedState s, unsigned* ctl) {
   extern __shared__ uint64_t smem[];
   Binom B = stage_binom(a, smem);
   const int lane = threadIdx.x & 31;
@@ -1034,9 +1541,12 @@ __global__ void __launch_bounds__(256) reduce_persistent_kernel(DimArgs a, RedSt
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t threads = gridDim.x * blockDim.x;
-  __shared__ uint64_t tile_key[WARPS_PER_BLOCK][SORT_TILE];
-  __shared__ uint32_t tile_coef[WARPS_PER_BLOCK][SORT_TILE];
-  const SortTile tile{tile_key[threadIdx.x >> 5], tile_coef[threadIdx.x >> 5]};
+  // the warps' sort tiles, or one merge tile for the whole block in block mode
+  __shared__ __align__(16) unsigned char red_smem[RED_SMEM_BYTES];
+  __shared__ MergeReq req;
+  const uint32_t w = threadIdx.x >> 5;
+  const SortTile tile{(uint64_t*)red_smem + w * SORT_TILE,
+                      (uint32_t*)(red_smem + (size_t)WARPS_PER_BLOCK * SORT_TILE * 8) + w * SORT_TILE};
   unsigned* claim_cnt = ctl;
   unsigned* red_cnt = ctl + 2;
   unsigned* bar_count = ctl + 4;
@@ -1057,8 +1567,12 @@ __global__ void __launch_bounds__(256) reduce_persistent_kernel(DimArgs a, RedSt
       red_cnt[dst] = 0;
     }
     const uint32_t nred = *(volatile unsigned*)&red_cnt[src];
-    for (uint32_t t = warp_id; t < nred; t += warps)
-      reduce_one(a, s, B, lane, tile, s.reduce_list[t], &claim_cnt[dst]);
+    if (nred <= gridDim.x) {  // few columns left: one block per column
+      if (blockIdx.x < nred) reduce_one_block(a, s, B, tile, red_smem, req, s.reduce_list[blockIdx.x], &claim_cnt[dst]);
+    } else {
+      for (uint32_t t = warp_id; t < nred; t += warps)
+        reduce_one(a, s, B, lane, tile, s.reduce_list[t], &claim_cnt[dst]);
+    }
     if (!grid_barrier(bar_count, bar_gen, a.err)) return;
   }
   if (tid == 0) ctl[6] = r;
@@ -1169,7 +1683,8 @@ int reduction_blocks(const DimArgs& a, uint32_t ncols) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reduce_persistent_kernel, 256, sm) != cudaSuccess)
     return -1;
   if (per_sm < 1) return -1;
-  uint64_t want = ((uint64_t)ncols + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
+  // as many blocks as fit, up to one per column: block mode takes one column per block
+  uint64_t want = ncols;
   uint64_t maxb = (uint64_t)sms * per_sm;
   int blocks = (int)(want < maxb ? want : maxb);
   return blocks < 1 ? 1 : blocks;
