@@ -561,6 +561,7 @@ int run_batch(Workspace& w, const float* dD, const std::vector<int64_t>& ns, int
       rs.steps = P<unsigned long long>(w.lists) + 4;
       rs.compacted = P<unsigned long long>(w.lists) + 5;
       rs.max_chain = counts + 7;
+      rs.heartbeat = counts + 12;
       rs.err = P<uint32_t>(w.err);
       {
         KTimer kt(w, RIPS_K_REDUCE, s);
@@ -574,7 +575,7 @@ int run_batch(Workspace& w, const float* dD, const std::vector<int64_t>& ns, int
       if (hp->u32[8] & ERRF_ARENA) {
         // start this dimension's reduction over with a larger arena
         CK(cudaMemsetAsync(w.err.p, 0, 4, s));
-        rcap *= 4;
+        rcap *= 8;
         continue;
       }
       if (int e = map_device_error(hp->u32[8])) return e;

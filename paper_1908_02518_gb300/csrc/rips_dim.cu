@@ -58,8 +58,15 @@ namespace rips {
 namespace {
 
 constexpr int WARPS_PER_BLOCK = 8;
-constexpr uint32_t MAX_PIVOT_PASSES = 1u << 18;  // cancellations in a row before giving up
+constexpr uint32_t MAX_PIVOT_PASSES = 1u << 30;  // additions in one chain before giving up
+constexpr unsigned long long CHAIN_LIMIT_NS = 600ull * 1000 * 1000 * 1000;  // or 10 min in one chain
 constexpr uint32_t WARP_CHAIN_LIMIT = 32;         // additions per round of a warp-reduced column
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 struct Binom {
   const uint64_t* t;
@@ -104,18 +111,48 @@ struct Simplex {
   uint32_t rank;
 };
 
+// largest v in [lo, hi] with C(v, k) <= N, by bisection
+__device__ __forceinline__ int max_vertex_bisect(const Binom& B, int k, int lo, int hi, uint64_t N) {
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (B(mid, k) <= N) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Largest v in [k-1, hi] with C(v, k) <= N (k >= 2), i.e. the top vertex of the
+// k-subset with index N (Section 4, "combinatorial number system").  Since
+// C(v, k) is about (v - (k-1)/2)^k / k!, a float root of k! N gives v to within
+// one or two; four neighbouring table entries (one or two cache lines) settle
+// it, and bisection takes over if the estimate was further off.
+__device__ __forceinline__ int max_vertex(const Binom& B, int k, int hi, uint64_t N) {
+  float kf = 1.0f;
+  for (int i = 2; i <= k; ++i) kf *= (float)i;
+  const float est = exp2f(log2f(__ull2float_rn(N) * kf) / (float)k) + 0.5f * (float)(k - 1);
+  int v = est >= (float)hi ? hi : (int)est;
+  if (v < k - 1) v = k - 1;
+  const uint64_t b0 = B(v, k);
+  const uint64_t bm = B(v > 0 ? v - 1 : 0, k);
+  const uint64_t b1 = B(v + 1 <= hi ? v + 1 : hi, k);
+  const uint64_t b2 = B(v + 2 <= hi ? v + 2 : hi, k);
+  if (b0 <= N) {
+    if (v == hi || b1 > N) return v;
+    if (v + 1 == hi || b2 > N) return v + 1;
+    return max_vertex_bisect(B, k, v + 2, hi, N);
+  }
+  // b0 > N implies v >= k, so v - 1 >= k - 1
+  if (bm <= N) return v - 1;
+  return max_vertex_bisect(B, k, k - 1, v - 2, N);
+}
+
 __device__ __forceinline__ void decode(const Binom& B, int n, uint64_t N, int d, int* v) {
   int hi = n - 1;
   for (int k = d + 1; k >= 1; --k) {
-    int lo = k - 1, h = hi;
-    while (lo < h) {
-      int mid = (lo + h + 1) >> 1;
-      if (B(mid, k) <= N) lo = mid;
-      else h = mid - 1;
-    }
-    v[d + 1 - k] = lo;
-    N -= B(lo, k);
-    hi = lo - 1;
+    const int x = k == 1 ? (int)N : max_vertex(B, k, hi, N);
+    v[d + 1 - k] = x;
+    N -= k == 1 ? N : B(x, k);
+    hi = x - 1;
   }
 }
 
@@ -849,6 +886,7 @@ struct Chain {
   int64_t owner;  // table owner of the pivot, or -1 to look it up
   bool started;   // R_j's own run is in place
   uint32_t pcoef; // block mode: pivot coefficient of the column being generated
+  unsigned long long t0;  // globaltimer when the chain passed 255 additions
 };
 
 enum : int { CH_DONE = 0, CH_MERGE = 1, CH_ARENA = 2, CH_LONG = 3, CH_INTERNAL = 4, CH_GEN = 5, CH_GEN_SELF = 6 };
@@ -862,12 +900,13 @@ struct ChainReq {
 
 // R_j <- R_j - lambda C, lambda = pivot coefficient ratio (Algorithm 1): the run
 // of C joins the set, then the new pivot is found
-__device__ __forceinline__ void chain_add(const DimArgs& a, Chain& ch, int lane, const uint64_t* wk,
-                                          const uint32_t* wc, uint32_t wn, uint32_t wcoef) {
+__device__ __forceinline__ void chain_add(const DimArgs& a, const RedState& s, Chain& ch, int lane,
+                                          const uint64_t* wk, const uint32_t* wc, uint32_t wn, uint32_t wcoef) {
   const uint32_t lam = (uint32_t)(((uint64_t)ch.coef * mod_inv(wcoef, a.p)) % a.p);
   if (lane == ch.nr) ch.r = make_run(wk, wc, wn, (a.p - lam) % a.p, a.p);
   ++ch.nr;
   ++ch.step;
+  if (lane == 0 && (ch.step & 15) == 0) atomicAdd(s.heartbeat, 1u);  // progress, for the grid barrier
   ch.key = runs_pivot(ch.r, a.p, &ch.coef);
   ch.owner = -1;
 }
@@ -904,6 +943,11 @@ __device__ int chain_advance(const DimArgs& a, const RedState& s, const CV& cv, 
     }
     if (ch.key == IDX_NONE) return CH_DONE;
     if (ch.step > MAX_PIVOT_PASSES) return CH_LONG;
+    if ((ch.step & 255) == 255) {  // the chain's wall-clock bound
+      const unsigned long long now = __shfl_sync(0xffffffffu, global_ns(), 0);
+      if (ch.t0 == 0) ch.t0 = now;
+      else if (now - ch.t0 > CHAIN_LIMIT_NS) return CH_LONG;
+    }
     if (block && !ch.started) {
       const uint32_t jn = s.r_len[j];
       if (!jn) {
@@ -973,7 +1017,7 @@ __device__ int chain_advance(const DimArgs& a, const RedState& s, const CV& cv, 
       ch.nr = 1;
       ch.started = true;
     }
-    chain_add(a, ch, lane, wk, wc, wn, wcoef);
+    chain_add(a, s, ch, lane, wk, wc, wn, wcoef);
   }
 }
 
@@ -1064,7 +1108,7 @@ __device__ void init_column(const DimArgs& a, const RedState& s, const Binom& B,
   }
   __syncwarp();
   // during the first phase the table is empty: only apparent facets can own a pivot
-  Chain ch{empty_run(), 0, 0, key, coef, -1, false, 0};
+  Chain ch{empty_run(), 0, 0, key, coef, -1, false, 0, 0};
   const int st = chain_warp(a, s, cv, B, lane, tile, j, idx, r, cl, ~0u, ch);
   if (st != CH_DONE) {
     chain_error(a, st);  // an arena overflow restarts this dimension with a larger arena
@@ -1105,7 +1149,7 @@ __device__ void reduce_one(const DimArgs& a, const RedState& s, const Binom& B, 
   uint32_t jr, cl;
   column_simplex(a, s, j, &jidx, &jr, &cl);
   const CV cv = cloud_view(a, cl);
-  Chain ch{empty_run(), 0, 0, s.piv_key[j], s.piv_coef[j], -1, false, 0};
+  Chain ch{empty_run(), 0, 0, s.piv_key[j], s.piv_coef[j], -1, false, 0, 0};
   ch.owner = reduce_owner(a, s, j, cl, ch.key);
   if (ch.owner < 0) {
     set_error(a.err, ERRF_INTERNAL);
@@ -1410,7 +1454,7 @@ __device__ void reduce_one_block(const DimArgs& a, const RedState& s, const Bino
   uint32_t jr, cl;
   column_simplex(a, s, j, &jidx, &jr, &cl);
   const CV cv = cloud_view(a, cl);
-  Chain ch{empty_run(), 0, 0, 0, 0, -1, false, 0};  // meaningful in warp 0 only
+  Chain ch{empty_run(), 0, 0, 0, 0, -1, false, 0, 0};  // meaningful in warp 0 only
   bool finishing = false;
   if (tid < 32) {
     ch.key = s.piv_key[j];
@@ -1472,7 +1516,7 @@ __device__ void reduce_one_block(const DimArgs& a, const RedState& s, const Bino
           ch.nr = 1;
           ch.started = true;
         } else {
-          chain_add(a, ch, lane, g.key, g.coef, g.len, ch.pcoef);
+          chain_add(a, s, ch, lane, g.key, g.coef, g.len, ch.pcoef);
         }
       }
     } else {
@@ -1487,18 +1531,14 @@ __device__ void reduce_one_block(const DimArgs& a, const RedState& s, const Bino
   chain_finish(s, ch, lane, j, claim_count);
 }
 
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
 constexpr unsigned long long BARRIER_LIMIT_NS = 30ull * 1000 * 1000 * 1000;  // 30 s
 
 // Grid-wide barrier for a cooperative launch (all blocks co-resident).  The
-// wait is bounded: past BARRIER_LIMIT_NS the block records ERRF_TIMEOUT and
-// returns false, and the caller leaves the kernel.
-__device__ bool grid_barrier(unsigned* count, unsigned* gen, uint32_t* err) {
+// wait is bounded: when BARRIER_LIMIT_NS pass with no block making progress
+// (the heartbeat counter, bumped by long chains of additions, stands still) the
+// block records ERRF_TIMEOUT and returns false, and the caller leaves the
+// kernel.
+__device__ bool grid_barrier(unsigned* count, unsigned* gen, const unsigned* heartbeat, uint32_t* err) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -1510,10 +1550,18 @@ __device__ bool grid_barrier(unsigned* count, unsigned* gen, uint32_t* err) {
       __threadfence();
       atomicAdd(gen, 1u);
     } else {
-      const unsigned long long t0 = global_ns();
+      unsigned long long t0 = global_ns();
+      unsigned hb = *(volatile const unsigned*)heartbeat;
       while (*(volatile unsigned*)gen == g) {
         __nanosleep(128);
-        if (global_ns() - t0 > BARRIER_LIMIT_NS) {
+        const unsigned long long now = global_ns();
+        if (now - t0 > BARRIER_LIMIT_NS) {
+          const unsigned h = *(volatile const unsigned*)heartbeat;
+          if (h != hb) {  // another block is still working
+            hb = h;
+            t0 = now;
+            continue;
+          }
           set_error(err, ERRF_TIMEOUT);
           ok = 0;
           break;
@@ -1532,7 +1580,8 @@ __device__ bool grid_barrier(unsigned* count, unsigned* gen, uint32_t* err) {
 // pivots of all columns, then claim / reduce rounds separated by grid
 // barriers, until no column is left to claim.  Work-list counters are double
 // buffered by round parity (ctl[0..1] claim, ctl[2..3] reduce); ctl[4..5] are
-// the barrier's counter and generation, ctl[6] receives the number of rounds.
+// the barrier's counter and generation, ctl[6] receives the number of rounds
+// and ctl[12] is the progress heartbeat.
 __global__ void __launch_bounds__(256, 3) reduce_persistent_kernel(DimArgs a, RedState s, unsigned* ctl) {
   extern __shared__ uint64_t smem[];
   Binom B = stage_binom(a, smem);
@@ -1553,7 +1602,7 @@ __global__ void __launch_bounds__(256, 3) reduce_persistent_kernel(DimArgs a, Re
   unsigned* bar_gen = ctl + 5;
 
   for (uint32_t j = warp_id; j < s.ncols; j += warps) init_column(a, s, B, lane, tile, j, &claim_cnt[0]);
-  if (!grid_barrier(bar_count, bar_gen, a.err)) return;
+  if (!grid_barrier(bar_count, bar_gen, s.heartbeat, a.err)) return;
   uint32_t r = 0;
   for (;; ++r) {
     const int src = r & 1, dst = src ^ 1;
@@ -1561,7 +1610,7 @@ __global__ void __launch_bounds__(256, 3) reduce_persistent_kernel(DimArgs a, Re
     const uint32_t errs = *(volatile uint32_t*)a.err;
     if (nclaim == 0 || (errs & (ERRF_ARENA | ERRF_TIMEOUT | ERRF_INTERNAL | ERRF_TABLE_FULL))) break;
     for (uint32_t t = tid; t < nclaim; t += threads) claim_one(a, s, s.claim_list[t], &red_cnt[src]);
-    if (!grid_barrier(bar_count, bar_gen, a.err)) return;
+    if (!grid_barrier(bar_count, bar_gen, s.heartbeat, a.err)) return;
     if (tid == 0) {
       claim_cnt[src] = 0;
       red_cnt[dst] = 0;
@@ -1573,7 +1622,7 @@ __global__ void __launch_bounds__(256, 3) reduce_persistent_kernel(DimArgs a, Re
       for (uint32_t t = warp_id; t < nred; t += warps)
         reduce_one(a, s, B, lane, tile, s.reduce_list[t], &claim_cnt[dst]);
     }
-    if (!grid_barrier(bar_count, bar_gen, a.err)) return;
+    if (!grid_barrier(bar_count, bar_gen, s.heartbeat, a.err)) return;
   }
   if (tid == 0) ctl[6] = r;
 }

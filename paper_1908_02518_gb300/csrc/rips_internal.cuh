@@ -198,6 +198,7 @@ struct RedState {
   unsigned long long* steps;
   unsigned long long* compacted;  // entries read by run compactions (profiling)
   uint32_t* max_chain;            // longest chain of additions (profiling)
+  unsigned* heartbeat;            // bumped while chains of additions make progress
   uint32_t* err;
 };
 
