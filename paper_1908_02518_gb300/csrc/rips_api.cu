@@ -96,6 +96,7 @@ struct Workspace {
   Buf piv_key, piv_coef, r_off, r_len, reduced, claim, reduce, lists;
   Buf r_key, r_coef, r_top;
   Buf tkeys[2], tvals[2];
+  Buf amk[2], amv[2];  // apparent-pair maps of dimensions d and d - 1
   Buf bars, bars_alt, bk0, bk1, bp0, bp1, bartmp, nbars;
   Buf stats, bwd_bars, bwd_off, cdist, clouds, tileoff, vcloud, ccounts;
   size_t r_cap = 0;
@@ -427,6 +428,8 @@ int run_batch(Workspace& w, const float* dD, const std::vector<int64_t>& ns, int
   int cur = 0;
   uint64_t* prev_tkeys = nullptr;
   uint64_t prev_tmask = 0;
+  const uint64_t* prev_amap = nullptr;
+  uint64_t prev_amask = 0;
   for (int d = 1; d <= dim_max; ++d) {
     DimArgs a;
     a.d = d;
@@ -445,6 +448,11 @@ int run_batch(Workspace& w, const float* dD, const std::vector<int64_t>& ns, int
     a.rank_bits = rank_bits;
     a.rank_max = num_ranks ? num_ranks - 1 : 0;
     a.err = P<uint32_t>(w.err);
+    a.amap_keys = nullptr;
+    a.amap_vals = nullptr;
+    a.amap_mask = 0;
+    a.pmap_keys = prev_amap;
+    a.pmap_mask = prev_amask;
     if (rank_bits + a.row_bits > 63 || cb + rank_bits + a.col_bits > 64 || cb + a.row_bits > 64)
       return RIPS_ERR_OVERFLOW;
     unsigned long long* st = dstats + d * 16;  // cloud c: st + c * SPC
@@ -488,6 +496,17 @@ int run_batch(Workspace& w, const float* dD, const std::vector<int64_t>& ns, int
     CR(ensure(w.ckeys_alt, (size_t)(nsd + 1) * 8));
     CR(ensure(w.ccount, 16));
     CK(cudaMemsetAsync(w.ccount.p, 0, 16, s));
+    // map of this dimension's zero apparent pairs (at most one per tested simplex)
+    uint64_t acap = 16;
+    while (acap < 2ull * nsd + 16) acap <<= 1;
+    if (a.col_bits <= 60 && acap * 16 <= (16ull << 30)) {  // else the test and reduction scan instead
+      CR(ensure(w.amk[cur], (size_t)acap * 8));
+      CR(ensure(w.amv[cur], (size_t)acap * 8));
+      CK(cudaMemsetAsync(w.amk[cur].p, 0xFF, (size_t)acap * 8, s));
+      a.amap_keys = P<uint64_t>(w.amk[cur]);
+      a.amap_vals = P<uint64_t>(w.amv[cur]);
+      a.amap_mask = acap - 1;
+    }
     {
       KTimer kt(w, RIPS_K_APPARENT, s);
       CK(launch_test(a, P<uint64_t>(w.sidx[cur]), P<uint32_t>(w.srank[cur]), nsd, P<uint8_t>(w.inforest), prev_tkeys,
@@ -596,6 +615,8 @@ int run_batch(Workspace& w, const float* dD, const std::vector<int64_t>& ns, int
     }
     if (!done) return RIPS_ERR_OOM;
     prev_tkeys = P<uint64_t>(w.tkeys[tb]);
+    prev_amap = a.amap_keys;
+    prev_amask = a.amap_mask;
     prev_tmask = tcap - 1;
     ns_prev = nsd;
     prev_col_bits = a.col_bits;

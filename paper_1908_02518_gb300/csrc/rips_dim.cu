@@ -423,6 +423,11 @@ __global__ void edges_to_simplices_kernel(const uint64_t* __restrict__ keys, con
 
 // ====================================================================== apparent + clearing test
 
+// pivot-table key of a row: (cloud << row_bits) | local row index
+__device__ __forceinline__ uint64_t table_key(const DimArgs& a, uint32_t cloud, uint64_t row_idx) {
+  return (a.row_bits >= 64 ? 0ull : ((uint64_t)cloud << a.row_bits)) | row_idx;
+}
+
 __global__ void __launch_bounds__(256) test_kernel(DimArgs a, const uint64_t* __restrict__ sidx,
                                                    const uint32_t* __restrict__ srank, uint32_t ns,
                                                    const uint8_t* __restrict__ cleared_flag /* d == 1 */,
@@ -489,14 +494,31 @@ __global__ void __launch_bounds__(256) test_kernel(DimArgs a, const uint64_t* __
       app = __shfl_sync(0xffffffffu, app, hl);
       if (app) {
         ++n_cof;
+        if (lane == 0 && a.amap_keys) {  // tau -> sigma, for the reduction and the next dimension
+          CofacetSums cs;
+          cofacet_sums(B, v, d, cs);
+          int c = 0;
+          for (int l = 0; l <= d; ++l) c += v[l] > j;
+          const uint64_t tidx = cs.above[c] + B(j, d + 2 - c) + cs.below[c];
+          const int64_t slot = table_insert(a.amap_keys, a.amap_mask, table_key(a, cl, tidx));
+          if (slot < 0) set_error(a.err, ERRF_TABLE_FULL);
+          else a.amap_vals[slot] = (idx << 4) | (uint64_t)c;
+        }
         continue;
       }
     }
-    // facet side (d >= 2; in dimension 1 such edges are spanning-forest edges)
+    // facet side (d >= 2; in dimension 1 such edges are spanning-forest edges):
+    // the previous dimension's test recorded every zero apparent pair
     if (d >= 2) {
-      uint32_t minus[MAX_DIM + 2];
-      ranks_minus_one(cv.R, cv.n, v, d, minus);
-      if (zero_apparent_facet(cv, v, d, r, minus, lane) >= 0) {
+      bool fac;
+      if (a.pmap_keys) {
+        fac = table_find(a.pmap_keys, a.pmap_mask, g) >= 0;
+      } else {
+        uint32_t minus[MAX_DIM + 2];
+        ranks_minus_one(cv.R, cv.n, v, d, minus);
+        fac = zero_apparent_facet(cv, v, d, r, minus, lane) >= 0;
+      }
+      if (fac) {
         ++n_fac;
         continue;
       }
@@ -528,10 +550,6 @@ __device__ __forceinline__ void column_simplex(const DimArgs& a, const RedState&
   *cloud = high_part(key, a.rank_bits + a.col_bits);
 }
 
-// pivot-table key of a row: (cloud << row_bits) | local row index
-__device__ __forceinline__ uint64_t table_key(const DimArgs& a, uint32_t cloud, uint64_t row_idx) {
-  return (a.row_bits >= 64 ? 0ull : ((uint64_t)cloud << a.row_bits)) | row_idx;
-}
 
 // Minimum over the cofacet entries of sum_{(s,c) in V} c * delta(s) restricted to
 // row keys > after: returns the key (IDX_NONE if none) and the summed
@@ -590,9 +608,17 @@ __device__ void min_entry(const DimArgs& a, const CV& cv, const Binom& B, int la
 
 // Apparent facet of the pivot row tau (a (d+1)-simplex): returns the facet index
 // (IDX_NONE if none), its rank and the coefficient of tau in its coboundary.
-__device__ uint64_t pivot_apparent_facet(const DimArgs& a, const CV& cv, const Binom& B, int lane, uint64_t key,
-                                         uint32_t* frank, uint32_t* tcoef) {
+__device__ uint64_t pivot_apparent_facet(const DimArgs& a, const CV& cv, const Binom& B, int lane, uint32_t cl,
+                                         uint64_t key, uint32_t* frank, uint32_t* tcoef) {
   const int k = a.d + 1;
+  if (a.amap_keys) {  // recorded by this dimension's test kernel
+    const int64_t slot = table_find(a.amap_keys, a.amap_mask, table_key(a, cl, row_key_idx(a, key)));
+    if (slot < 0) return IDX_NONE;
+    const uint64_t v = a.amap_vals[slot];
+    *frank = row_key_rank(a, key);
+    *tcoef = ((a.d - (int)(v & 15)) & 1) ? a.p - 1 : 1u;
+    return v >> 4;
+  }
   const uint64_t tidx = row_key_idx(a, key);
   const uint32_t tr = row_key_rank(a, key);
   int w[MAX_DIM + 2];
@@ -706,27 +732,43 @@ struct Run {
   const uint32_t* coef;
   uint32_t len, cur, scale;
   uint64_t hk;  // head key, ~0 once the run is used up
-  uint32_t hc;  // head coefficient times scale, mod p
+  uint32_t hc;  // head coefficient times scale, mod p (1 over Z/2)
+  uint64_t nk;  // the key after the head, loaded ahead of time
 };
 
+// head coefficient (over Z/2 every stored coefficient is 1)
+__device__ __forceinline__ uint32_t run_coef(const Run& r, uint32_t p) {
+  return p == 2 ? 1u : (uint32_t)(((uint64_t)r.coef[r.cur] * r.scale) % p);
+}
+
 __device__ __forceinline__ void run_head(Run& r, uint32_t p) {
-  if (r.cur < r.len) {
-    r.hk = r.key[r.cur];
-    r.hc = (uint32_t)(((uint64_t)r.coef[r.cur] * r.scale) % p);
-  } else {
-    r.hk = ~0ull;
-    r.hc = 0;
-  }
+  r.hk = r.cur < r.len ? r.key[r.cur] : ~0ull;
+  r.hc = r.cur < r.len ? run_coef(r, p) : 0u;
+  r.nk = r.cur + 1 < r.len ? r.key[r.cur + 1] : ~0ull;
+}
+
+// move to the next entry; its key was loaded ahead, the one after is requested now
+__device__ __forceinline__ void run_next(Run& r, uint32_t p) {
+  ++r.cur;
+  r.hk = r.nk;
+  r.hc = r.cur < r.len ? run_coef(r, p) : 0u;
+  r.nk = r.cur + 1 < r.len ? r.key[r.cur + 1] : ~0ull;
 }
 
 __device__ __forceinline__ Run make_run(const uint64_t* k, const uint32_t* c, uint32_t n, uint32_t scale,
                                         uint32_t p) {
-  Run r{k, c, n, 0, scale, ~0ull, 0};
+  Run r{k, c, n, 0, scale, ~0ull, 0, ~0ull};
   run_head(r, p);
   return r;
 }
 
-__device__ __forceinline__ Run empty_run() { return Run{nullptr, nullptr, 0, 0, 1, ~0ull, 0}; }
+__device__ __forceinline__ Run empty_run() { return Run{nullptr, nullptr, 0, 0, 1, ~0ull, 0, ~0ull}; }
+
+// combined coefficient of the lanes at the current minimum (`at`)
+__device__ __forceinline__ uint32_t warp_coef_sum(bool at, uint32_t hc, uint32_t p) {
+  if (p == 2) return __popc(__ballot_sync(0xffffffffu, at)) & 1u;
+  return __reduce_add_sync(0xffffffffu, at ? hc : 0u) % p;
+}
 
 // size class of the run's remaining entries (-1 when used up)
 __device__ __forceinline__ int run_tier(const Run& r) {
@@ -800,15 +842,12 @@ __device__ uint64_t runs_pivot(Run& r, uint32_t p, uint32_t* coef_out) {
       return IDX_NONE;
     }
     const bool at = r.hk == m;
-    const uint32_t c = __reduce_add_sync(0xffffffffu, at ? r.hc : 0u) % p;
+    const uint32_t c = warp_coef_sum(at, r.hc, p);
     if (c) {
       *coef_out = c;
       return m;
     }
-    if (at) {
-      ++r.cur;
-      run_head(r, p);
-    }
+    if (at) run_next(r, p);
   }
 }
 
@@ -825,6 +864,7 @@ __device__ void runs_pack(Run& r, int lane, int* nr) {
   t.scale = __shfl_sync(0xffffffffu, r.scale, src);
   t.hk = __shfl_sync(0xffffffffu, r.hk, src);
   t.hc = __shfl_sync(0xffffffffu, r.hc, src);
+  t.nk = __shfl_sync(0xffffffffu, r.nk, src);
   r = lane < cnt ? t : empty_run();
   *nr = cnt;
 }
@@ -856,11 +896,8 @@ __device__ bool runs_merge_warp(const RedState& s, Run& r, int lane, uint32_t p,
     const uint64_t m = warp_min_u64(h);
     if (m == ~0ull) break;
     const bool at = h == m;
-    const uint32_t c = __reduce_add_sync(0xffffffffu, at ? r.hc : 0u) % p;
-    if (at) {
-      ++r.cur;
-      run_head(r, p);
-    }
+    const uint32_t c = warp_coef_sum(at, r.hc, p);
+    if (at) run_next(r, p);
     if (c) {
       if (lane == 0) {
         ok[out] = m;
@@ -965,7 +1002,7 @@ __device__ int chain_advance(const DimArgs& a, const RedState& s, const CV& cv, 
     uint32_t wn, wcoef;
     if (ch.owner < 0) {
       uint32_t frank, tcoef;
-      const uint64_t fidx = pivot_apparent_facet(a, cv, B, lane, ch.key, &frank, &tcoef);
+      const uint64_t fidx = pivot_apparent_facet(a, cv, B, lane, cl, ch.key, &frank, &tcoef);
       if (fidx == IDX_NONE) {
         const int64_t slot = table_find(s.t_keys, s.t_mask, table_key(a, cl, row_key_idx(a, ch.key)));
         const uint32_t k = slot >= 0 ? s.t_vals[slot] : 0xFFFFFFFFu;
@@ -1229,10 +1266,12 @@ __device__ void block_bitonic(uint64_t* key, uint32_t* coef, uint32_t n2) {
 
 // Coboundary of the d-simplex (idx, rank) generated by the whole block: each
 // thread tests one neighbour of the simplex's vertex with the fewest
-// neighbours, a block scan packs the cofacets, a bitonic network sorts them in
-// shared memory (in an arena buffer when more than GEN_SMEM_CAP are possible),
-// and they are stored in the arena.  *out gets the run (scale 1).  Called by
-// the whole block; false (in every thread) when the arena is full.
+// neighbours and a block scan packs the cofacets into shared memory.  Up to
+// blockDim.x cofacets are then placed by rank (each thread counts the smaller
+// keys; the keys are distinct) straight into their arena slots, reserved at
+// the start; more are sorted by a bitonic network (in an arena buffer past
+// GEN_SMEM_CAP) and copied.  *out gets the run (scale 1).  Called by the whole
+// block; false (in every thread) when the arena is full.
 __device__ bool block_gen_sorted(const DimArgs& a, const RedState& s, const CV& cv, const Binom& B,
                                  unsigned char* raw, MergeReq& q, uint64_t idx, uint32_t rank, RunDesc* out) {
   const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -1243,18 +1282,20 @@ __device__ bool block_gen_sorted(const DimArgs& a, const RedState& s, const CV& 
   cofacet_sums(B, v, d, cs);
   const int av = v[min_degree_vertex(cv, v, d + 1)];
   const uint32_t beg = cv.off[av], end = cv.off[av + 1];
+  const uint32_t deg = end - beg;  // at most this many cofacets
   uint32_t p2 = 1;
-  while (p2 < end - beg) p2 <<= 1;
+  while (p2 < deg) p2 <<= 1;
+  const bool in_arena = p2 > GEN_SMEM_CAP;
+  // the output slots (and the sort buffer when it does not fit in shared memory)
+  const unsigned long long want = in_arena ? p2 : (deg ? deg : 1);
+  if (tid == 0) q.off = atomicAdd(s.r_top, want);
   uint64_t* bk = (uint64_t*)raw;
   uint32_t* bc = (uint32_t*)(raw + (size_t)GEN_SMEM_CAP * 8);
-  const bool in_arena = p2 > GEN_SMEM_CAP;
   if (in_arena) {
-    if (tid == 0) q.off = atomicAdd(s.r_top, (unsigned long long)p2);
     __syncthreads();
-    const unsigned long long off = q.off;
-    if (off + p2 > s.r_cap) return false;
-    bk = s.r_key + off;
-    bc = s.r_coef + off;
+    if (q.off + want > s.r_cap) return false;
+    bk = s.r_key + q.off;
+    bc = s.r_coef + q.off;
   }
   uint32_t cnt = 0;
   for (uint32_t q0 = beg; q0 < end; q0 += blockDim.x) {
@@ -1280,6 +1321,21 @@ __device__ bool block_gen_sorted(const DimArgs& a, const RedState& s, const CV& 
     cnt += tot;
     __syncthreads();  // wsum is reused
   }
+  if (beg == end) __syncthreads();  // q.off is read below
+  const unsigned long long off = q.off;
+  if (off + want > s.r_cap) return false;
+  if (!in_arena && cnt <= blockDim.x) {
+    if (tid < cnt) {  // rank placement
+      const uint64_t k = bk[tid];
+      uint32_t rk = 0;
+      for (uint32_t u = 0; u < cnt; ++u) rk += bk[u] < k;
+      s.r_key[off + rk] = k;
+      s.r_coef[off + rk] = bc[tid];
+    }
+    __syncthreads();
+    *out = RunDesc{s.r_key + off, s.r_coef + off, cnt, 1};
+    return true;
+  }
   uint32_t n2 = 1;
   while (n2 < cnt) n2 <<= 1;
   for (uint32_t i = cnt + tid; i < n2; i += blockDim.x) {
@@ -1292,10 +1348,6 @@ __device__ bool block_gen_sorted(const DimArgs& a, const RedState& s, const CV& 
     *out = RunDesc{bk, bc, cnt, 1};
     return true;
   }
-  if (tid == 0) q.off = atomicAdd(s.r_top, (unsigned long long)(cnt ? cnt : 1));
-  __syncthreads();
-  const unsigned long long off = q.off;
-  if (off + cnt > s.r_cap) return false;
   for (uint32_t i = tid; i < cnt; i += blockDim.x) {
     s.r_key[off + i] = bk[i];
     s.r_coef[off + i] = bc[i];
@@ -1447,7 +1499,6 @@ __device__ bool block_merge_runs(const RedState& s, MergeSmem& ms, MergeReq& q, 
 // when warp 0 asks for it.  The chain has no step limit here.
 __device__ void reduce_one_block(const DimArgs& a, const RedState& s, const Binom& B, const SortTile& tile,
                                  unsigned char* raw, MergeReq& q, uint32_t j, uint32_t* claim_count) {
-  MergeSmem& ms = *(MergeSmem*)raw;
   const uint32_t tid = threadIdx.x;
   const int lane = tid & 31;
   uint64_t jidx;
@@ -1494,7 +1545,7 @@ __device__ void reduce_one_block(const DimArgs& a, const RedState& s, const Bino
     __syncthreads();
     state = q.state;
     if (state == CH_MERGE) {
-      if (!block_merge_runs(s, ms, q, a.p)) {
+      if (!block_merge_runs(s, *(MergeSmem*)raw, q, a.p)) {
         state = CH_ARENA;
         break;
       }

@@ -168,6 +168,16 @@ struct DimArgs {
   int rank_bits;                   // bits of a diameter rank
   uint32_t rank_max;               // largest diameter rank
   uint32_t* err;
+  // zero-persistence apparent pairs (sigma, tau) with sigma a d-simplex, written
+  // by the test kernel: key (cloud << row_bits) | idx(tau), value
+  // (idx(sigma) << 4) | position of the vertex tau has beyond sigma; null when
+  // col_bits > 60 (the index does not fit beside the position)
+  uint64_t* amap_keys;
+  uint64_t* amap_vals;
+  uint64_t amap_mask;
+  // the same map of dimension d - 1 (keys (cloud << col_bits) | idx(sigma)), or null
+  const uint64_t* pmap_keys;
+  uint64_t pmap_mask;
 };
 
 // Reduction state (device pointers) shared by the reduction kernels
