@@ -41,6 +41,9 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--profile", action="store_true",
                     help="warm-up calls then exactly one barcode call, for ncu launch lists and captures")
+    ap.add_argument("--dim-max", type=int, default=None, help="override the workload's top dimension")
+    ap.add_argument("--batched", action="store_true",
+                    help="256 ragged clouds: batched forward+backward against a per-cloud loop of the same path")
     return ap.parse_args()
 
 
@@ -104,6 +107,98 @@ def peaks():
         return float(p["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def kernel_roofline(name, km, stats, n, peak, peak_kind):
+    """HBM roofline of one kernel class: algorithmic bytes per launch (the
+    per-unit figures in the design doc times the units one launch processes) over the
+    class's average launch time, both from the CUDA-event kernel timing."""
+    if name not in km or km[name][0] <= 0:
+        return None
+    launches = max(km[name][1], 1)
+    dims = stats[1:]
+    if name == "apparent":    # S2: read (index 8 B + rank 4 B) per tested simplex, write 8 B per column,
+        algo = sum(12 * s["simplices"] + 8 * s["columns"] + 16 * s["apparent_cofacet"] for s in dims)
+    elif name == "reduce":    # S5: read 12 B per entry of every added column, 32 B of state per column
+        algo = sum(12 * s["added_entries"] + 32 * s["columns"] for s in dims)
+    elif name == "enumerate":  # S1: write 12 B (index + rank) per simplex of dimension >= 2
+        algo = sum(12 * s["simplices"] for s in stats[2:])
+    elif name == "col_sort":   # S3: 8 radix passes reading and writing 8 B keys
+        algo = sum(8 * 16 * s["columns"] for s in dims)
+    elif name == "prologue":   # S0: read D once, write the rank matrix once
+        algo = 8 * n * n
+    else:
+        return None
+    algo /= launches
+    ms = km[name][0] / launches
+    achieved = algo / (ms / 1000.0) / 1e9
+    return {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind, "launch_ms": ms,
+            "algorithmic_bytes": algo, "launches_per_step": launches}
+
+
+def run_batched(args):
+    """Forward + backward of loss = sum over H1 bars of (death - birth)^2 over
+    the 256 ragged clouds (64..512 points: circles, tori, cubes): one batched
+    call against a loop of the same GPU path called per cloud, both timed with
+    CUDA events, inputs resident on the device."""
+    import torch
+    import paper_1908_02518_gb300 as rg
+    from paper_1908_02518_gb300 import workloads as W
+    clouds = W.batch_clouds()
+    sizes = [len(c) for c in clouds]
+    offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    pts = torch.from_numpy(np.concatenate(clouds)).cuda()
+    dev_clouds = [pts[offsets[i]:offsets[i + 1]] for i in range(len(clouds))]
+    stream = torch.cuda.current_stream()
+
+    def step(x, off):
+        res = rg.barcodes_batched(x, off, 1, math.inf, 2, keep_handle=True)
+        b = res.bars
+        h1 = (b["dim"] == 1) & np.isfinite(b["death"])
+        diff = np.where(h1, b["death"] - b["birth"], 0.0).astype(np.float32)
+        gb = torch.from_numpy(-2.0 * diff).cuda()
+        gd = torch.from_numpy(2.0 * diff).cuda()
+        g = rg.backward(res, x, gb, gd)
+        loss = float((diff.astype(np.float64) ** 2).sum())
+        units = sum(s["simplices"] for st in res.stats for s in st)
+        res.free()
+        return g, loss, units
+
+    def timed(fn, reps):
+        out = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            r = fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            out.append(a.elapsed_time(b))
+        return statistics.median(out), r
+
+    for _ in range(max(args.warmup, 1)):
+        step(pts, offsets)
+    t_batch, (gx, loss, units) = timed(lambda: step(pts, offsets), max(args.steps // 4, 3))
+
+    def loop():
+        gs, ls, us = [], 0.0, 0
+        for x in dev_clouds:
+            g, l_, u = step(x, np.array([0, len(x)], dtype=np.int64))
+            gs.append(g)
+            ls += l_
+            us += u
+        return torch.cat(gs), ls, us
+    loop()
+    t_loop, (gl, loss_l, units_l) = timed(loop, 3)
+    same = bool(torch.equal(gx, gl)) and loss == loss_l
+    print(json.dumps({"metric": "batched_forward_backward_ms", "value": t_batch, "unit": "ms",
+                      "higher_is_better": False, "per_cloud_loop_ms": t_loop, "speedup": t_loop / t_batch,
+                      "clouds": len(clouds), "points": int(offsets[-1]), "simplices": units,
+                      "simplices_per_s": units / (t_batch / 1000.0), "loss": loss,
+                      "gradients_identical_to_loop": same, "dtype": "f32 coordinates; integer ranks",
+                      "data": "synthetic", "config": {"workload": "batch256", "dim_max": 1, "p": 2}}))
+    return 0
 
 
 def cpu_baseline(w, budget_s=12.0):
@@ -170,7 +265,11 @@ def main():
     from paper_1908_02518_gb300 import _lib
     lib = _lib.load()
 
+    if args.batched:
+        return run_batched(args)
     w = load_workload(args.workload)
+    if args.dim_max is not None:
+        w.dim_max = args.dim_max
     n = w.n
     dev_d = torch.from_numpy(w.dist).cuda()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -240,27 +339,16 @@ def main():
     rg.set_kernel_timing(False)
     dom = max(km, key=lambda x: km[x][0])
     stats = res.stats[0]
-    # algorithmic bytes of the dominant kernel class per timed region
-    algo_bytes = None
-    if dom == "apparent":
-        tested = sum(s["simplices"] for s in stats[1:])
-        cols = sum(s["columns"] for s in stats[1:])
-        algo_bytes = (12 * tested + 8 * cols) / max(km[dom][1], 1)
-    elif dom == "reduce":
-        cols = sum(s["columns"] for s in stats[1:])
-        algo_bytes = 24 * cols / max(km[dom][1], 1)
-    elif dom == "prologue":
-        algo_bytes = (4 * n * n + 4 * n * n) / max(km[dom][1], 1)
-    elif dom == "enumerate":
-        algo_bytes = sum(12 * s["simplices"] for s in stats[2:]) / max(km[dom][1], 1)
     peak, peak_kind = peaks()
-    roof = None
-    if algo_bytes is not None and km[dom][0] > 0:
-        per_region_ms = km[dom][0] / max(km[dom][1], 1)
-        achieved = algo_bytes / (per_region_ms / 1000.0) / 1e9
-        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                "region_ms": per_region_ms, "algorithmic_bytes": algo_bytes}
+    roof = kernel_roofline(dom, km, stats, n, peak, peak_kind)
+    streaming = kernel_roofline("apparent", km, stats, n, peak, peak_kind)
+    if dom == "reduce":
+        # the reduction is bound by its longest chain of dependent additions
+        worst = max(range(1, len(stats)), key=lambda d: stats[d]["longest_chain"]) if len(stats) > 1 else 0
+        chain = stats[worst]["longest_chain"] if worst else 0
+        dim_ms = statistics.median(p[worst] for p in phase) if worst else 0.0
+        roof["critical_path"] = {"dim": worst, "longest_chain": chain, "dim_phase_ms": dim_ms,
+                                 "us_per_chain_addition": 1000.0 * dim_ms / chain if chain else None}
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     pinned = torch.from_numpy(w.dist).pin_memory()
@@ -291,7 +379,8 @@ def main():
                            "l2": "flushed between steps (256 MiB write)"},
                 "per_dim": per_dim, "barcode_ms": ms_per_step, "bars": nbars,
                 "kernel_ms": {k: v[0] for k, v in km.items()},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": ck}
+                "roofline": roof, "roofline_streaming": streaming, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": ck}
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -86,6 +86,7 @@ typedef struct rips_stats {
   int64_t rounds;           /* claim/reduce rounds of the reduction */
   int64_t longest_chain;    /* most additions made by one column in one round */
   int64_t compacted_entries;/* working-column entries merged by run compactions */
+  int64_t added_entries;    /* entries of the columns added to working columns, summed */
 } rips_stats_t;
 
 typedef struct rips_result rips_result_t;

@@ -26,7 +26,7 @@ class Stats(C.Structure):
                 ("cleared", C.c_int64), ("columns", C.c_int64), ("emergent", C.c_int64),
                 ("pairs", C.c_int64), ("zero_pairs", C.c_int64), ("essential", C.c_int64),
                 ("reduction_steps", C.c_int64), ("rounds", C.c_int64), ("longest_chain", C.c_int64),
-                ("compacted_entries", C.c_int64)]
+                ("compacted_entries", C.c_int64), ("added_entries", C.c_int64)]
 
 
 # every symbol declared in include/rips.h

@@ -581,6 +581,7 @@ int run_batch(Workspace& w, const float* dD, const std::vector<int64_t>& ns, int
       rs.compacted = P<unsigned long long>(w.lists) + 5;
       rs.max_chain = counts + 7;
       rs.heartbeat = counts + 12;
+      rs.added = P<unsigned long long>(w.lists) + 7;
       rs.err = P<uint32_t>(w.err);
       {
         KTimer kt(w, RIPS_K_REDUCE, s);
@@ -589,6 +590,7 @@ int run_batch(Workspace& w, const float* dD, const std::vector<int64_t>& ns, int
       CK(cudaMemcpyAsync(&hp->u32[6], counts + 6, 4, cudaMemcpyDeviceToHost, s));
       CK(cudaMemcpyAsync(&hp->u32[8], w.err.p, 4, cudaMemcpyDeviceToHost, s));
       CK(cudaMemcpyAsync(&hp->u64[1], rs.steps, 16, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(&hp->u64[3], rs.added, 8, cudaMemcpyDeviceToHost, s));
       CK(cudaMemcpyAsync(&hp->u32[9], counts + 7, 4, cudaMemcpyDeviceToHost, s));
       CR(sync_read(w, s));
       if (hp->u32[8] & ERRF_ARENA) {
@@ -605,6 +607,7 @@ int run_batch(Workspace& w, const float* dD, const std::vector<int64_t>& ns, int
         out.stats[(size_t)c * (dim_max + 1) + d].reduction_steps = (int64_t)hp->u64[1];
         out.stats[(size_t)c * (dim_max + 1) + d].longest_chain = hp->u32[9];
         out.stats[(size_t)c * (dim_max + 1) + d].compacted_entries = (int64_t)hp->u64[2];
+        out.stats[(size_t)c * (dim_max + 1) + d].added_entries = (int64_t)hp->u64[3];
       }
       {
         KTimer kt(w, RIPS_K_READOUT, s);

@@ -943,7 +943,10 @@ __device__ __forceinline__ void chain_add(const DimArgs& a, const RedState& s, C
   if (lane == ch.nr) ch.r = make_run(wk, wc, wn, (a.p - lam) % a.p, a.p);
   ++ch.nr;
   ++ch.step;
-  if (lane == 0 && (ch.step & 15) == 0) atomicAdd(s.heartbeat, 1u);  // progress, for the grid barrier
+  if (lane == 0) {
+    atomicAdd(s.added, (unsigned long long)wn);
+    if ((ch.step & 15) == 0) atomicAdd(s.heartbeat, 1u);  // progress, for the grid barrier
+  }
   ch.key = runs_pivot(ch.r, a.p, &ch.coef);
   ch.owner = -1;
 }

@@ -209,6 +209,7 @@ struct RedState {
   unsigned long long* compacted;  // entries read by run compactions (profiling)
   uint32_t* max_chain;            // longest chain of additions (profiling)
   unsigned* heartbeat;            // bumped while chains of additions make progress
+  unsigned long long* added;      // entries of the columns added (profiling)
   uint32_t* err;
 };
 

@@ -40,16 +40,10 @@ def _key_gold(bars):
     return sorted((d, b, e, bs, U64MAX if ds < 0 else ds) for d, b, e, bs, ds in bars)
 
 
-HEAVY = {"s3_192", "so3_4096"}
-
-
 @pytest.mark.parametrize("name", ["cube100", "torus1000", "s3_192", "so3_4096"])
 def test_workload_matches_golden(name):
-    import os as _os
     import torch
     import paper_1908_02518_gb300 as rg
-    if name in HEAVY and _os.environ.get("RIPS_HEAVY_GOLDEN") != "1":
-        pytest.skip("long single-column reduction chains: run with RIPS_HEAVY_GOLDEN=1")
     head, bars = _read(name)
     w = W.WORKLOADS[name]()
     assert W.matrix_digest(w.dist) == head["sha256"], "input generator is not bit-identical on this host"
