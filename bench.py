@@ -191,12 +191,16 @@ def run_batched(args):
         return torch.cat(gs), ls, us
     loop()
     t_loop, (gl, loss_l, units_l) = timed(loop, 3)
-    same = bool(torch.equal(gx, gl)) and loss == loss_l
+    # the backward scatter adds with float atomics, so the order of additions
+    # (and the last bits) differ between the two; compare within 1e-4 relative
+    gdiff = float((gx - gl).abs().max())
+    gscale = max(float(gl.abs().max()), 1e-6)
     print(json.dumps({"metric": "batched_forward_backward_ms", "value": t_batch, "unit": "ms",
                       "higher_is_better": False, "per_cloud_loop_ms": t_loop, "speedup": t_loop / t_batch,
                       "clouds": len(clouds), "points": int(offsets[-1]), "simplices": units,
                       "simplices_per_s": units / (t_batch / 1000.0), "loss": loss,
-                      "gradients_identical_to_loop": same, "dtype": "f32 coordinates; integer ranks",
+                      "loss_close_to_loop": math.isclose(loss, loss_l, rel_tol=1e-9), "grad_max_rel_diff_to_loop": gdiff / gscale,
+                      "grad_within_1e-4": gdiff <= 1e-4 * gscale, "dtype": "f32 coordinates; integer ranks",
                       "data": "synthetic", "config": {"workload": "batch256", "dim_max": 1, "p": 2}}))
     return 0
 

@@ -93,7 +93,7 @@ struct Workspace {
   Buf eu, ev, comp, best, parent, gtop, inforest, fpos, nf;
   Buf sidx[2], srank[2], scount;
   Buf ckeys, ckeys_alt, ccount, sorttmp;
-  Buf piv_key, piv_coef, r_off, r_len, reduced, claim, reduce, lists;
+  Buf piv_key, piv_coef, r_off, r_len, reduced, claim, reduce, heavy, lists;
   Buf r_key, r_coef, r_top;
   Buf tkeys[2], tvals[2];
   Buf amk[2], amv[2];  // apparent-pair maps of dimensions d and d - 1
@@ -541,7 +541,8 @@ int run_batch(Workspace& w, const float* dD, const std::vector<int64_t>& ns, int
     CR(ensure(w.reduced, (size_t)(M + 1)));
     CR(ensure(w.claim, (size_t)(M + 1) * 4));
     CR(ensure(w.reduce, (size_t)(M + 1) * 4));
-    CR(ensure(w.lists, 64));
+    CR(ensure(w.heavy, (size_t)(M + 1) * 8));
+    CR(ensure(w.lists, 128));
     CR(ensure(w.r_top, 16));
     // a generated coboundary holds at most max_deg entries (sorted in a power-of-two buffer)
     const int blocks = M ? reduction_blocks(a, M) : 1;
@@ -556,7 +557,7 @@ int run_batch(Workspace& w, const float* dD, const std::vector<int64_t>& ns, int
       w.r_cap = rcap;
       CK(cudaMemsetAsync(w.tkeys[tb].p, 0xFF, (size_t)tcap * 8, s));
       CK(cudaMemsetAsync(w.tvals[tb].p, 0xFF, (size_t)tcap * 4, s));
-      CK(cudaMemsetAsync(w.lists.p, 0, 64, s));
+      CK(cudaMemsetAsync(w.lists.p, 0, 128, s));
       CK(cudaMemsetAsync(w.r_top.p, 0, 16, s));
       uint32_t* counts = P<uint32_t>(w.lists);
       RedState rs;
@@ -577,6 +578,7 @@ int run_batch(Workspace& w, const float* dD, const std::vector<int64_t>& ns, int
       rs.t_mask = tcap - 1;
       rs.claim_list = P<uint32_t>(w.claim);
       rs.reduce_list = P<uint32_t>(w.reduce);
+      rs.heavy_list = P<uint32_t>(w.heavy);
       rs.steps = P<unsigned long long>(w.lists) + 4;
       rs.compacted = P<unsigned long long>(w.lists) + 5;
       rs.max_chain = counts + 7;

@@ -60,7 +60,9 @@ namespace {
 constexpr int WARPS_PER_BLOCK = 8;
 constexpr uint32_t MAX_PIVOT_PASSES = 1u << 30;  // additions in one chain before giving up
 constexpr unsigned long long CHAIN_LIMIT_NS = 600ull * 1000 * 1000 * 1000;  // or 10 min in one chain
-constexpr uint32_t WARP_CHAIN_LIMIT = 32;         // additions per round of a warp-reduced column
+constexpr uint32_t WARP_CHAIN_LIMIT = 32;         // additions before a warp-reduced column turns heavy
+constexpr uint32_t WARP_MERGE_MAX = 2048;         // largest merge a warp makes; larger ones turn it heavy
+constexpr uint8_t HEAVY = 2;                      // flag in RedState::reduced: reduced block-wide
 
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
@@ -926,7 +928,8 @@ struct Chain {
   unsigned long long t0;  // globaltimer when the chain passed 255 additions
 };
 
-enum : int { CH_DONE = 0, CH_MERGE = 1, CH_ARENA = 2, CH_LONG = 3, CH_INTERNAL = 4, CH_GEN = 5, CH_GEN_SELF = 6 };
+enum : int { CH_DONE = 0, CH_MERGE = 1, CH_ARENA = 2, CH_LONG = 3, CH_INTERNAL = 4, CH_GEN = 5, CH_GEN_SELF = 6,
+             CH_HEAVY = 7 };
 
 // work handed from warp 0 to its block: runs to merge, or a coboundary to generate
 struct ChainReq {
@@ -956,10 +959,10 @@ __device__ __forceinline__ void chain_add(const DimArgs& a, const RedState& s, C
 // Sections 3.1 and 3.4).  Owners found in the table are stable while the
 // reduce phase runs (an owner is never on the reduce list), so the chain may
 // take several steps in one round.  A pivot with a zero apparent facet is owned
-// by that facet's column (Section 4, "Persistence pairs").  After `limit`
-// additions the chain stops at the next pivot owned by an earlier column in the
-// table (never at an apparent facet's pivot, which no column may claim); the
-// column then claims that pivot again, loses, and is reduced in a later round.
+// by that facet's column (Section 4, "Persistence pairs").  In warp mode a
+// chain longer than `limit` additions, or one needing a merge of more than
+// WARP_MERGE_MAX entries, stops with CH_HEAVY before anything is written back:
+// the column is then reduced block-wide from its last stored state.
 // In warp mode (block == false) the warp merges runs and generates coboundaries
 // itself.  In block mode these are handed back to the block: CH_MERGE with the
 // lanes of the runs, CH_GEN with the simplex whose coboundary is to be added
@@ -977,6 +980,8 @@ __device__ int chain_advance(const DimArgs& a, const RedState& s, const CV& cv, 
         req->mask = mm;
         return CH_MERGE;
       }
+      if (__reduce_add_sync(0xffffffffu, (mm >> lane) & 1u ? ch.r.len - ch.r.cur : 0u) > WARP_MERGE_MAX)
+        return CH_HEAVY;
       if (!runs_merge_warp(s, ch.r, lane, a.p, mm)) return CH_ARENA;
       runs_pack(ch.r, lane, &ch.nr);
       continue;
@@ -1009,8 +1014,8 @@ __device__ int chain_advance(const DimArgs& a, const RedState& s, const CV& cv, 
       if (fidx == IDX_NONE) {
         const int64_t slot = table_find(s.t_keys, s.t_mask, table_key(a, cl, row_key_idx(a, ch.key)));
         const uint32_t k = slot >= 0 ? s.t_vals[slot] : 0xFFFFFFFFu;
-        if (k >= j) return CH_DONE;           // free, or owned by a later column: claim it next round
-        if (ch.step >= limit) return CH_DONE;  // long chain: the next round goes on with it
+        if (k >= j) return CH_DONE;             // free, or owned by a later column: claim it next round
+        if (ch.step >= limit) return CH_HEAVY;  // long chain: a block takes the column over
         ch.owner = k;
         continue;
       }
@@ -1079,7 +1084,7 @@ __device__ void chain_finish(const RedState& s, const Chain& ch, int lane, uint3
   const uint32_t len = __shfl_sync(0xffffffffu, r.len - r.cur, src & 31);
   if (lane != 0) return;
   if (ch.step) {
-    s.reduced[j] = 1;
+    s.reduced[j] |= 1;
     atomicAdd(s.steps, (unsigned long long)ch.step);
     atomicMax(s.max_chain, ch.step);
     if (ch.key != IDX_NONE) {
@@ -1101,11 +1106,23 @@ __device__ int chain_warp(const DimArgs& a, const RedState& s, const CV& cv, con
   if (ch.step && ch.key != IDX_NONE) {
     const unsigned m = chain_store_mask(ch, lane);
     if (m) {
+      if (__reduce_add_sync(0xffffffffu, (m >> lane) & 1u ? ch.r.len - ch.r.cur : 0u) > WARP_MERGE_MAX)
+        return CH_HEAVY;
       if (!runs_merge_warp(s, ch.r, lane, a.p, m)) return CH_ARENA;
       runs_pack(ch.r, lane, &ch.nr);
     }
   }
   return CH_DONE;
+}
+
+// A warp gives a heavy column up before changing any of its state: the column
+// is flagged and queued for a block in the next round.
+__device__ __forceinline__ void chain_give_up(const RedState& s, int lane, uint32_t j, uint32_t* heavy_count,
+                                              uint32_t* heavy_list) {
+  if (lane == 0) {
+    s.reduced[j] |= HEAVY;
+    heavy_list[atomicAdd(heavy_count, 1u)] = j;
+  }
 }
 
 __device__ __forceinline__ void chain_error(const DimArgs& a, int st) {
@@ -1118,7 +1135,7 @@ __device__ __forceinline__ void chain_error(const DimArgs& a, int st) {
 // oldest entry.  A pivot with a zero apparent facet is eliminated at once.  A
 // column with a pivot is appended to the claim list.
 __device__ void init_column(const DimArgs& a, const RedState& s, const Binom& B, int lane, const SortTile& tile,
-                            uint32_t j, uint32_t* claim_count) {
+                            uint32_t j, uint32_t* claim_count, uint32_t* heavy_count, uint32_t* heavy_list) {
   const int d = a.d;
   uint64_t idx;
   uint32_t r, cl;
@@ -1150,6 +1167,14 @@ __device__ void init_column(const DimArgs& a, const RedState& s, const Binom& B,
   // during the first phase the table is empty: only apparent facets can own a pivot
   Chain ch{empty_run(), 0, 0, key, coef, -1, false, 0, 0};
   const int st = chain_warp(a, s, cv, B, lane, tile, j, idx, r, cl, ~0u, ch);
+  if (st == CH_HEAVY) {  // the block will start over from the first pivot
+    if (lane == 0) {
+      s.piv_key[j] = key;
+      s.piv_coef[j] = coef;
+    }
+    chain_give_up(s, lane, j, heavy_count, heavy_list);
+    return;
+  }
   if (st != CH_DONE) {
     chain_error(a, st);  // an arena overflow restarts this dimension with a larger arena
     return;
@@ -1159,7 +1184,14 @@ __device__ void init_column(const DimArgs& a, const RedState& s, const Binom& B,
 
 // Column j claims its pivot: the smallest ordinal owns it; the loser (j, or the
 // displaced former owner) goes to the reduce list.
-__device__ void claim_one(const DimArgs& a, const RedState& s, uint32_t j, uint32_t* reduce_count) {
+__device__ __forceinline__ void to_reduce(const RedState& s, uint32_t j, uint32_t* reduce_count, uint32_t* heavy_count,
+                                          uint32_t* heavy_list) {
+  if (s.reduced[j] & HEAVY) heavy_list[atomicAdd(heavy_count, 1u)] = j;
+  else s.reduce_list[atomicAdd(reduce_count, 1u)] = j;
+}
+
+__device__ void claim_one(const DimArgs& a, const RedState& s, uint32_t j, uint32_t* reduce_count,
+                          uint32_t* heavy_count, uint32_t* heavy_list) {
   const uint64_t key = s.piv_key[j];
   const uint32_t cl = high_part(s.col_keys[j], a.rank_bits + a.col_bits);
   const int64_t slot = table_insert(s.t_keys, s.t_mask, table_key(a, cl, row_key_idx(a, key)));
@@ -1168,8 +1200,8 @@ __device__ void claim_one(const DimArgs& a, const RedState& s, uint32_t j, uint3
     return;
   }
   const uint32_t old = atomicMin(&s.t_vals[slot], j);
-  if (old < j) s.reduce_list[atomicAdd(reduce_count, 1u)] = j;
-  else if (old != 0xFFFFFFFFu && old != j) s.reduce_list[atomicAdd(reduce_count, 1u)] = old;
+  if (old < j) to_reduce(s, j, reduce_count, heavy_count, heavy_list);
+  else if (old != 0xFFFFFFFFu && old != j) to_reduce(s, old, reduce_count, heavy_count, heavy_list);
 }
 
 // owner of column j's current pivot in the table, which must precede j
@@ -1184,7 +1216,7 @@ __device__ __forceinline__ int64_t reduce_owner(const DimArgs& a, const RedState
 // this round, one warp, at most WARP_CHAIN_LIMIT additions, and goes back to
 // the claim list unless it became zero.
 __device__ void reduce_one(const DimArgs& a, const RedState& s, const Binom& B, int lane, const SortTile& tile,
-                           uint32_t j, uint32_t* claim_count) {
+                           uint32_t j, uint32_t* claim_count, uint32_t* heavy_count, uint32_t* heavy_list) {
   uint64_t jidx;
   uint32_t jr, cl;
   column_simplex(a, s, j, &jidx, &jr, &cl);
@@ -1196,6 +1228,10 @@ __device__ void reduce_one(const DimArgs& a, const RedState& s, const Binom& B, 
     return;
   }
   const int st = chain_warp(a, s, cv, B, lane, tile, j, jidx, jr, cl, WARP_CHAIN_LIMIT, ch);
+  if (st == CH_HEAVY) {
+    chain_give_up(s, lane, j, heavy_count, heavy_list);
+    return;
+  }
   if (st != CH_DONE) {
     chain_error(a, st);
     return;
@@ -1241,6 +1277,7 @@ struct MergeReq {
   uint32_t grank;
   uint32_t wsum[WARPS_PER_BLOCK];
   unsigned long long off;
+  uint32_t take;  // the heavy column this block takes next
 };
 
 constexpr uint32_t GEN_SMEM_CAP = (uint32_t)(RED_SMEM_BYTES / 12);  // generated entries sorted in shared memory
@@ -1497,9 +1534,10 @@ __device__ bool block_merge_runs(const RedState& s, MergeSmem& ms, MergeReq& q, 
   return true;
 }
 
-// Column j of the reduce list, reduced by the whole block (see block mode):
-// warp 0 runs the chain, and the block generates coboundaries and merges runs
-// when warp 0 asks for it.  The chain has no step limit here.
+// Column j, reduced by the whole block (see block mode): warp 0 runs the chain,
+// and the block generates coboundaries and merges runs when warp 0 asks for it.
+// The chain has no step limit here.  A heavy column given up by a warp may come
+// with a pivot nobody owns yet; the chain then ends at once and claims it.
 __device__ void reduce_one_block(const DimArgs& a, const RedState& s, const Binom& B, const SortTile& tile,
                                  unsigned char* raw, MergeReq& q, uint32_t j, uint32_t* claim_count) {
   const uint32_t tid = threadIdx.x;
@@ -1520,8 +1558,7 @@ __device__ void reduce_one_block(const DimArgs& a, const RedState& s, const Bino
     if (tid < 32) {
       ChainReq cr{0u, 0ull, 0u};
       int st = CH_DONE;
-      if (ch.owner < 0 && ch.step == 0) st = CH_INTERNAL;
-      else if (!finishing) st = chain_advance(a, s, cv, B, lane, tile, j, jidx, jr, cl, ~0u, true, ch, &cr);
+      if (!finishing) st = chain_advance(a, s, cv, B, lane, tile, j, jidx, jr, cl, ~0u, true, ch, &cr);
       if (st == CH_DONE && !finishing) {  // the chain ended: R_j must become one run
         finishing = true;
         if (ch.step && ch.key != IDX_NONE) {
@@ -1632,11 +1669,15 @@ __device__ bool grid_barrier(unsigned* count, unsigned* gen, const unsigned* hea
 
 // The whole reduction of one dimension in one cooperative launch: the first
 // pivots of all columns, then claim / reduce rounds separated by grid
-// barriers, until no column is left to claim.  Work-list counters are double
-// buffered by round parity (ctl[0..1] claim, ctl[2..3] reduce); ctl[4..5] are
-// the barrier's counter and generation, ctl[6] receives the number of rounds
-// and ctl[12] is the progress heartbeat.
-__global__ void __launch_bounds__(256, 3) reduce_persistent_kernel(DimArgs a, RedState s, unsigned* ctl) {
+// barriers, until no column is left to claim or reduce.  The losers of a
+// round's claims are reduced in its reduce phase: heavy columns (flagged when a
+// warp gave them up) one block each, the others one warp each, both handed out
+// by atomic counters; when all fit, every column gets a block.  Work-list
+// counters are double buffered by round parity (ctl[0..1] claim, ctl[2..3]
+// reduce, ctl[16..17] heavy); ctl[4..5] are the barrier's counter and
+// generation, ctl[6] receives the number of rounds, ctl[12] is the progress
+// heartbeat and ctl[18..19] the light and heavy work cursors.
+__global__ void __launch_bounds__(256, 2) reduce_persistent_kernel(DimArgs a, RedState s, unsigned* ctl) {
   extern __shared__ uint64_t smem[];
   Binom B = stage_binom(a, smem);
   const int lane = threadIdx.x & 31;
@@ -1654,27 +1695,57 @@ __global__ void __launch_bounds__(256, 3) reduce_persistent_kernel(DimArgs a, Re
   unsigned* red_cnt = ctl + 2;
   unsigned* bar_count = ctl + 4;
   unsigned* bar_gen = ctl + 5;
+  unsigned* heavy_cnt = ctl + 16;
+  unsigned* light_next = ctl + 18;
+  unsigned* heavy_next = ctl + 19;
+  uint32_t* heavy[2] = {s.heavy_list, s.heavy_list + (size_t)s.ncols + 1};
 
-  for (uint32_t j = warp_id; j < s.ncols; j += warps) init_column(a, s, B, lane, tile, j, &claim_cnt[0]);
+  for (uint32_t j = warp_id; j < s.ncols; j += warps)
+    init_column(a, s, B, lane, tile, j, &claim_cnt[0], &heavy_cnt[0], heavy[0]);
   if (!grid_barrier(bar_count, bar_gen, s.heartbeat, a.err)) return;
   uint32_t r = 0;
   for (;; ++r) {
     const int src = r & 1, dst = src ^ 1;
     const uint32_t nclaim = *(volatile unsigned*)&claim_cnt[src];
+    const uint32_t nqueued = *(volatile unsigned*)&heavy_cnt[src];
     const uint32_t errs = *(volatile uint32_t*)a.err;
-    if (nclaim == 0 || (errs & (ERRF_ARENA | ERRF_TIMEOUT | ERRF_INTERNAL | ERRF_TABLE_FULL))) break;
-    for (uint32_t t = tid; t < nclaim; t += threads) claim_one(a, s, s.claim_list[t], &red_cnt[src]);
+    if ((nclaim == 0 && nqueued == 0) || (errs & (ERRF_ARENA | ERRF_TIMEOUT | ERRF_INTERNAL | ERRF_TABLE_FULL)))
+      break;
+    for (uint32_t t = tid; t < nclaim; t += threads)
+      claim_one(a, s, s.claim_list[t], &red_cnt[src], &heavy_cnt[src], heavy[src]);
+    if (tid == 0) {  // the next round's heavy list and this round's cursors start empty
+      heavy_cnt[dst] = 0;
+      *light_next = 0;
+      *heavy_next = 0;
+    }
     if (!grid_barrier(bar_count, bar_gen, s.heartbeat, a.err)) return;
     if (tid == 0) {
       claim_cnt[src] = 0;
       red_cnt[dst] = 0;
     }
     const uint32_t nred = *(volatile unsigned*)&red_cnt[src];
-    if (nred <= gridDim.x) {  // few columns left: one block per column
-      if (blockIdx.x < nred) reduce_one_block(a, s, B, tile, red_smem, req, s.reduce_list[blockIdx.x], &claim_cnt[dst]);
+    const uint32_t nheavy = *(volatile unsigned*)&heavy_cnt[src];
+    if (nred + nheavy <= gridDim.x) {  // few columns left: one block per column
+      const uint32_t t = blockIdx.x;
+      if (t < nheavy) reduce_one_block(a, s, B, tile, red_smem, req, heavy[src][t], &claim_cnt[dst]);
+      else if (t < nheavy + nred)
+        reduce_one_block(a, s, B, tile, red_smem, req, s.reduce_list[t - nheavy], &claim_cnt[dst]);
     } else {
-      for (uint32_t t = warp_id; t < nred; t += warps)
-        reduce_one(a, s, B, lane, tile, s.reduce_list[t], &claim_cnt[dst]);
+      for (;;) {  // heavy columns: a block each
+        if (threadIdx.x == 0) req.take = atomicAdd(heavy_next, 1u);
+        __syncthreads();
+        const uint32_t t = req.take;
+        __syncthreads();
+        if (t >= nheavy) break;
+        reduce_one_block(a, s, B, tile, red_smem, req, heavy[src][t], &claim_cnt[dst]);
+      }
+      for (;;) {  // the others: a warp each
+        uint32_t t = 0;
+        if (lane == 0) t = atomicAdd(light_next, 1u);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= nred) break;
+        reduce_one(a, s, B, lane, tile, s.reduce_list[t], &claim_cnt[dst], &heavy_cnt[dst], heavy[dst]);
+      }
     }
     if (!grid_barrier(bar_count, bar_gen, s.heartbeat, a.err)) return;
   }
@@ -1697,7 +1768,7 @@ __global__ void readout_kernel(DimArgs a, RedState s, const float* __restrict__ 
     b.cloud = (int32_t)cl;
     b.birth = rank_value[r];
     b.birth_simplex = idx;
-    if (!s.reduced[j] && key != IDX_NONE) atomicAdd(&st[3], 1ull);
+    if (s.reduced[j] == 0 && key != IDX_NONE) atomicAdd(&st[3], 1ull);
     if (key == IDX_NONE) {
       atomicAdd(&st[2], 1ull);
       b.death = __int_as_float(0x7f800000);

@@ -205,6 +205,7 @@ struct RedState {
   // work lists
   uint32_t* claim_list;
   uint32_t* reduce_list;
+  uint32_t* heavy_list;           // two lists of M entries: columns reduced block-wide, by round parity
   unsigned long long* steps;
   unsigned long long* compacted;  // entries read by run compactions (profiling)
   uint32_t* max_chain;            // longest chain of additions (profiling)
