@@ -220,6 +220,30 @@ RIPS_API const char* rips_status_string(int status);
  * since the last reset (a profiling aid). */
 RIPS_API int64_t rips_kernel_launch_count(int reset);
 
+/* Launch and scheduling parameters of one dimension's kernels.  The paper has
+ * no counterpart: these are implementation choices, and no setting changes any
+ * result (bars and statistics other than timings are identical).  They are
+ * looked up per dimension d >= 1 and per the largest cloud size n of a call. */
+typedef struct rips_tuning {
+  int32_t warp_chain_limit;     /* additions one warp makes on a column before a block takes it over (>= 1) */
+  int32_t warp_merge_max;       /* largest merge of working-column runs one warp makes (>= 1) */
+  int32_t reduce_blocks_per_sm; /* blocks per SM of the reduction (0: as many as fit) */
+  int32_t scan_blocks_per_sm;   /* blocks per SM of the enumeration and test kernels (1..64) */
+} rips_tuning_t;
+
+/* Use `t` for dimension `dim` (1..7) when the largest cloud of a call has
+ * n_lo <= n <= n_hi points.  Entries added later take precedence.  The table
+ * is process-wide and guarded by a lock.  RIPS_ERR_BAD_ARG on out-of-range
+ * fields. */
+RIPS_API int rips_set_tuning(int32_t dim, int64_t n_lo, int64_t n_hi, const rips_tuning_t* t);
+
+/* The parameters a call with largest cloud size n would use in dimension dim
+ * (the built-in defaults when no entry matches). */
+RIPS_API int rips_get_tuning(int32_t dim, int64_t n, rips_tuning_t* out);
+
+/* Forget every entry (back to the built-in defaults). */
+RIPS_API void rips_clear_tuning(void);
+
 #ifdef __cplusplus
 }
 #endif

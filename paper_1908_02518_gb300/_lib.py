@@ -29,13 +29,18 @@ class Stats(C.Structure):
                 ("compacted_entries", C.c_int64), ("added_entries", C.c_int64)]
 
 
+class Tuning(C.Structure):
+    _fields_ = [("warp_chain_limit", C.c_int32), ("warp_merge_max", C.c_int32),
+                ("reduce_blocks_per_sm", C.c_int32), ("scan_blocks_per_sm", C.c_int32)]
+
+
 # every symbol declared in include/rips.h
 EXPORTS = [
     "rips_barcodes", "rips_barcodes_device", "rips_distance_matrix_device", "rips_barcodes_batched",
     "rips_barcodes_backward", "rips_result_num_bars", "rips_result_bars", "rips_result_num_clouds",
     "rips_result_dim_max", "rips_result_threshold", "rips_result_stats", "rips_result_phase_ms",
     "rips_result_free", "rips_status_string", "rips_kernel_launch_count", "rips_set_kernel_timing",
-    "rips_result_kernel_ms", "rips_h0_barcode_noalloc",
+    "rips_result_kernel_ms", "rips_h0_barcode_noalloc", "rips_set_tuning", "rips_get_tuning", "rips_clear_tuning",
 ]
 
 KERNEL_CLASSES = ["prologue", "edge_sort", "h0", "enumerate", "apparent", "col_sort", "pivot_init", "reduce",
@@ -94,6 +99,12 @@ def load(build_if_missing: bool = True):
     lib.rips_result_kernel_ms.restype = C.c_int
     lib.rips_h0_barcode_noalloc.argtypes = [vp, i64, C.c_float, vp, vp, vp]
     lib.rips_h0_barcode_noalloc.restype = C.c_int
+    lib.rips_set_tuning.argtypes = [i32, i64, i64, C.POINTER(Tuning)]
+    lib.rips_set_tuning.restype = C.c_int
+    lib.rips_get_tuning.argtypes = [i32, i64, C.POINTER(Tuning)]
+    lib.rips_get_tuning.restype = C.c_int
+    lib.rips_clear_tuning.argtypes = []
+    lib.rips_clear_tuning.restype = None
     _lib = lib
     return lib
 

@@ -185,6 +185,28 @@ struct rips_result {
 
 using namespace rips;
 
+// ------------------------------------------------------------------ tuning table
+// Launch and scheduling parameters per (dimension, largest cloud size), set by
+// the autotuner or the caller; the defaults are the values that serve the test
+// workloads well.
+namespace {
+struct TuneEntry {
+  int32_t dim;
+  int64_t lo, hi;
+  rips_tuning_t t;
+};
+std::mutex g_tune_mu;
+std::vector<TuneEntry> g_tune;
+constexpr rips_tuning_t TUNE_DEFAULT{32, 2048, 0, 16};
+
+rips_tuning_t tuning_for(int dim, int64_t n) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  for (auto it = g_tune.rbegin(); it != g_tune.rend(); ++it)
+    if (it->dim == dim && n >= it->lo && n <= it->hi) return it->t;
+  return TUNE_DEFAULT;
+}
+}  // namespace
+
 namespace {
 
 #define CK(x)                                      \
@@ -453,6 +475,13 @@ int run_batch(Workspace& w, const float* dD, const std::vector<int64_t>& ns, int
     a.amap_mask = 0;
     a.pmap_keys = prev_amap;
     a.pmap_mask = prev_amask;
+    {
+      const rips_tuning_t tu = tuning_for(d, n_max);
+      a.chain_limit = (uint32_t)tu.warp_chain_limit;
+      a.merge_max = (uint32_t)tu.warp_merge_max;
+      a.reduce_blocks_per_sm = tu.reduce_blocks_per_sm;
+      a.scan_blocks_per_sm = tu.scan_blocks_per_sm;
+    }
     if (rank_bits + a.row_bits > 63 || cb + rank_bits + a.col_bits > 64 || cb + a.row_bits > 64)
       return RIPS_ERR_OVERFLOW;
     unsigned long long* st = dstats + d * 16;  // cloud c: st + c * SPC
@@ -951,6 +980,27 @@ RIPS_API int64_t rips_kernel_launch_count(int reset) {
   long long v = g_launches;
   if (reset) g_launches = 0;
   return v;
+}
+
+RIPS_API int rips_set_tuning(int32_t dim, int64_t n_lo, int64_t n_hi, const rips_tuning_t* t) {
+  if (!t || dim < 1 || dim > 7 || n_lo < 1 || n_hi < n_lo) return RIPS_ERR_BAD_ARG;
+  if (t->warp_chain_limit < 1 || t->warp_merge_max < 1 || t->reduce_blocks_per_sm < 0 ||
+      t->scan_blocks_per_sm < 1 || t->scan_blocks_per_sm > 64)
+    return RIPS_ERR_BAD_ARG;
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  g_tune.push_back(TuneEntry{dim, n_lo, n_hi, *t});
+  return RIPS_OK;
+}
+
+RIPS_API int rips_get_tuning(int32_t dim, int64_t n, rips_tuning_t* out) {
+  if (!out || dim < 1 || dim > 7 || n < 1) return RIPS_ERR_BAD_ARG;
+  *out = tuning_for(dim, n);
+  return RIPS_OK;
+}
+
+RIPS_API void rips_clear_tuning(void) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  g_tune.clear();
 }
 
 RIPS_API int rips_barcodes_batched(const float* d_points, const int64_t* offsets, int32_t batch, int32_t k,

@@ -31,7 +31,7 @@
 //                     pivot with a zero apparent facet is owned by that facet's
 //                     column (Section 4, "Persistence pairs": apparent pairs are
 //                     not in the table).  A warp reduces a column while there
-//                     are more columns than blocks, for at most WARP_CHAIN_LIMIT
+//                     are more columns than blocks, for at most DimArgs::chain_limit
 //                     additions a round; with fewer, a block takes each column
 //                     and adds with a block-wide merge, which is what long
 //                     chains of additions need.
@@ -60,8 +60,6 @@ namespace {
 constexpr int WARPS_PER_BLOCK = 8;
 constexpr uint32_t MAX_PIVOT_PASSES = 1u << 30;  // additions in one chain before giving up
 constexpr unsigned long long CHAIN_LIMIT_NS = 600ull * 1000 * 1000 * 1000;  // or 10 min in one chain
-constexpr uint32_t WARP_CHAIN_LIMIT = 32;         // additions before a warp-reduced column turns heavy
-constexpr uint32_t WARP_MERGE_MAX = 2048;         // largest merge a warp makes; larger ones turn it heavy
 constexpr uint8_t HEAVY = 2;                      // flag in RedState::reduced: reduced block-wide
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -961,7 +959,7 @@ __device__ __forceinline__ void chain_add(const DimArgs& a, const RedState& s, C
 // take several steps in one round.  A pivot with a zero apparent facet is owned
 // by that facet's column (Section 4, "Persistence pairs").  In warp mode a
 // chain longer than `limit` additions, or one needing a merge of more than
-// WARP_MERGE_MAX entries, stops with CH_HEAVY before anything is written back:
+// DimArgs::merge_max entries, stops with CH_HEAVY before anything is written back:
 // the column is then reduced block-wide from its last stored state.
 // In warp mode (block == false) the warp merges runs and generates coboundaries
 // itself.  In block mode these are handed back to the block: CH_MERGE with the
@@ -980,7 +978,7 @@ __device__ int chain_advance(const DimArgs& a, const RedState& s, const CV& cv, 
         req->mask = mm;
         return CH_MERGE;
       }
-      if (__reduce_add_sync(0xffffffffu, (mm >> lane) & 1u ? ch.r.len - ch.r.cur : 0u) > WARP_MERGE_MAX)
+      if (__reduce_add_sync(0xffffffffu, (mm >> lane) & 1u ? ch.r.len - ch.r.cur : 0u) > a.merge_max)
         return CH_HEAVY;
       if (!runs_merge_warp(s, ch.r, lane, a.p, mm)) return CH_ARENA;
       runs_pack(ch.r, lane, &ch.nr);
@@ -1106,7 +1104,7 @@ __device__ int chain_warp(const DimArgs& a, const RedState& s, const CV& cv, con
   if (ch.step && ch.key != IDX_NONE) {
     const unsigned m = chain_store_mask(ch, lane);
     if (m) {
-      if (__reduce_add_sync(0xffffffffu, (m >> lane) & 1u ? ch.r.len - ch.r.cur : 0u) > WARP_MERGE_MAX)
+      if (__reduce_add_sync(0xffffffffu, (m >> lane) & 1u ? ch.r.len - ch.r.cur : 0u) > a.merge_max)
         return CH_HEAVY;
       if (!runs_merge_warp(s, ch.r, lane, a.p, m)) return CH_ARENA;
       runs_pack(ch.r, lane, &ch.nr);
@@ -1213,7 +1211,7 @@ __device__ __forceinline__ int64_t reduce_owner(const DimArgs& a, const RedState
 }
 
 // Column j (its pivot owned by an earlier column) reduces as far as it can in
-// this round, one warp, at most WARP_CHAIN_LIMIT additions, and goes back to
+// this round, one warp, at most DimArgs::chain_limit additions, and goes back to
 // the claim list unless it became zero.
 __device__ void reduce_one(const DimArgs& a, const RedState& s, const Binom& B, int lane, const SortTile& tile,
                            uint32_t j, uint32_t* claim_count, uint32_t* heavy_count, uint32_t* heavy_list) {
@@ -1227,7 +1225,7 @@ __device__ void reduce_one(const DimArgs& a, const RedState& s, const Binom& B, 
     set_error(a.err, ERRF_INTERNAL);
     return;
   }
-  const int st = chain_warp(a, s, cv, B, lane, tile, j, jidx, jr, cl, WARP_CHAIN_LIMIT, ch);
+  const int st = chain_warp(a, s, cv, B, lane, tile, j, jidx, jr, cl, a.chain_limit, ch);
   if (st == CH_HEAVY) {
     chain_give_up(s, lane, j, heavy_count, heavy_list);
     return;
@@ -1790,9 +1788,22 @@ __global__ void readout_kernel(DimArgs a, RedState s, const float* __restrict__ 
 
 // ---------------------------------------------------------------- host launchers
 
-static int grid_for_warps(uint64_t items) {
+static int sm_count() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess || sms < 1)
+      sms = 152;
+  }
+  return sms;
+}
+
+// one warp per item, at most per_sm blocks on every SM (the rest loop)
+static int grid_for_warps(uint64_t items, int per_sm) {
   uint64_t blocks = (items + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
-  if (blocks > 152ull * 16) blocks = 152ull * 16;
+  const uint64_t cap = (uint64_t)sm_count() * (uint64_t)(per_sm > 0 ? per_sm : 16);
+  if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   return (int)blocks;
 }
@@ -1820,7 +1831,7 @@ cudaError_t launch_enumerate(const DimArgs& a, const uint64_t* pidx, const uint3
   size_t sm = binom_smem(a);
   cudaError_t e = prepare(enumerate_kernel, sm);
   if (e != cudaSuccess) return e;
-  enumerate_kernel<<<grid_for_warps(np), 256, sm, st>>>(a, pidx, prank, np, prev_col_bits, out_idx, out_rank, count,
+  enumerate_kernel<<<grid_for_warps(np, a.scan_blocks_per_sm), 256, sm, st>>>(a, pidx, prank, np, prev_col_bits, out_idx, out_rank, count,
                                                         cap);
   note_launch();
   return cudaGetLastError();
@@ -1842,7 +1853,7 @@ cudaError_t launch_test(const DimArgs& a, const uint64_t* sidx, const uint32_t* 
   size_t sm = binom_smem(a);
   cudaError_t e = prepare(test_kernel, sm);
   if (e != cudaSuccess) return e;
-  test_kernel<<<grid_for_warps(ns), 256, sm, st>>>(a, sidx, srank, ns, cleared_flag, prev_keys, prev_mask, col_keys,
+  test_kernel<<<grid_for_warps(ns, a.scan_blocks_per_sm), 256, sm, st>>>(a, sidx, srank, ns, cleared_flag, prev_keys, prev_mask, col_keys,
                                                    ncols, col_cap, stats, stats_stride);
   note_launch();
   return cudaGetLastError();
@@ -1859,6 +1870,7 @@ int reduction_blocks(const DimArgs& a, uint32_t ncols) {
   if (per_sm < 1) return -1;
   // as many blocks as fit, up to one per column: block mode takes one column per block
   uint64_t want = ncols;
+  if (a.reduce_blocks_per_sm > 0 && a.reduce_blocks_per_sm < per_sm) per_sm = a.reduce_blocks_per_sm;
   uint64_t maxb = (uint64_t)sms * per_sm;
   int blocks = (int)(want < maxb ? want : maxb);
   return blocks < 1 ? 1 : blocks;

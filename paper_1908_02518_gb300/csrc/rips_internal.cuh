@@ -178,6 +178,11 @@ struct DimArgs {
   // the same map of dimension d - 1 (keys (cloud << col_bits) | idx(sigma)), or null
   const uint64_t* pmap_keys;
   uint64_t pmap_mask;
+  // launch and scheduling parameters (rips_tuning_t)
+  uint32_t chain_limit;            // additions a warp makes on one column before a block takes it
+  uint32_t merge_max;              // largest run merge one warp makes
+  int reduce_blocks_per_sm;        // 0: occupancy limit
+  int scan_blocks_per_sm;
 };
 
 // Reduction state (device pointers) shared by the reduction kernels
