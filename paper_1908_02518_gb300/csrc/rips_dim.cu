@@ -1258,6 +1258,7 @@ struct MergeSmem {
 };
 constexpr size_t RED_SMEM_BYTES = (size_t)WARPS_PER_BLOCK * SORT_TILE * 12;  // the warps' sort tiles
 static_assert(sizeof(MergeSmem) <= RED_SMEM_BYTES, "merge tile overlays the sort tiles");
+static_assert(2 * WARPS_PER_BLOCK * 32 * 24 <= RED_SMEM_BYTES, "small merge fits the sort tiles");
 
 struct RunDesc {
   const uint64_t* key;
@@ -1503,9 +1504,86 @@ __device__ uint32_t block_axpy(MergeSmem& ms, const RunDesc& A, const RunDesc& B
 // The runs of a merge request, summed two at a time (a tree of block_axpy)
 // into q.d[0] with scale 1.  Called by the whole block; false (in every
 // thread) when the arena is full.
+constexpr uint32_t SMALL_MERGE = 2 * WARPS_PER_BLOCK * 32;  // entries merged in one shared-memory pass
+
+// The request's runs when they hold at most SMALL_MERGE entries together: all
+// entries are loaded into shared memory at once, each is placed by its rank
+// (smaller keys, then equal keys loaded before it), the first of every group of
+// equal keys takes the group's coefficient sum, and a block scan packs the
+// nonzero ones into the arena.  One pass instead of a tree of tile merges.
+__device__ bool block_merge_small(const RedState& s, unsigned char* raw, MergeReq& q, uint32_t p, uint32_t total) {
+  const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  uint64_t* sk = (uint64_t*)raw;                                       // loaded keys
+  uint64_t* ok = (uint64_t*)(raw + SMALL_MERGE * 8);                   // sorted keys
+  uint32_t* sc = (uint32_t*)(raw + SMALL_MERGE * 16);                  // loaded coefficients (scaled)
+  uint32_t* oc = (uint32_t*)(raw + SMALL_MERGE * 16 + SMALL_MERGE * 4);  // sorted coefficients
+  if (tid == 0) q.off = atomicAdd(s.r_top, (unsigned long long)(total ? total : 1));
+  for (uint32_t e = tid; e < total; e += blockDim.x) {
+    uint32_t r = 0, pre = 0;
+    while (e >= pre + q.d[r].len) pre += q.d[r++].len;
+    const RunDesc& R = q.d[r];
+    sk[e] = R.key[e - pre];
+    sc[e] = R.scale == 1 ? R.coef[e - pre] : (uint32_t)(((uint64_t)R.coef[e - pre] * R.scale) % p);
+  }
+  __syncthreads();
+  for (uint32_t e = tid; e < total; e += blockDim.x) {
+    const uint64_t k = sk[e];
+    uint32_t rk = 0;
+    for (uint32_t u = 0; u < total; ++u) {
+      const uint64_t x = sk[u];
+      rk += x < k || (x == k && u < e);
+    }
+    ok[rk] = k;
+    oc[rk] = sc[e];
+  }
+  __syncthreads();
+  uint64_t kk[2];
+  uint32_t vv[2];
+  uint32_t cnt = 0;
+  for (uint32_t x = 2 * tid; x < 2 * tid + 2 && x < total; ++x) {
+    if (x > 0 && ok[x - 1] == ok[x]) continue;  // summed into the group's first entry
+    uint32_t c = 0;
+    for (uint32_t y = x; y < total && ok[y] == ok[x]; ++y) c = (c + oc[y]) % p;
+    if (c) {
+      kk[cnt] = ok[x];
+      vv[cnt] = c;
+      ++cnt;
+    }
+  }
+  uint32_t incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= (uint32_t)o) incl += t;
+  }
+  if (lane == 31) q.wsum[wid] = incl;
+  __syncthreads();
+  uint32_t base = 0, kept = 0;
+  for (uint32_t w = 0; w < WARPS_PER_BLOCK; ++w) {
+    if (w < wid) base += q.wsum[w];
+    kept += q.wsum[w];
+  }
+  const unsigned long long off = q.off;
+  if (off + total > s.r_cap) return false;
+  for (uint32_t e = 0; e < cnt; ++e) {
+    s.r_key[off + base + incl - cnt + e] = kk[e];
+    s.r_coef[off + base + incl - cnt + e] = vv[e];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    q.d[0] = RunDesc{s.r_key + off, s.r_coef + off, kept, 1};
+    atomicAdd(s.compacted, (unsigned long long)total);
+  }
+  __syncthreads();
+  return true;
+}
+
 __device__ bool block_merge_runs(const RedState& s, MergeSmem& ms, MergeReq& q, uint32_t p) {
   const RunDesc none{nullptr, nullptr, 0, 1};
   uint32_t n = q.n;
+  uint32_t total = 0;
+  for (uint32_t i = 0; i < n; ++i) total += q.d[i].len;
+  if (total <= SMALL_MERGE) return block_merge_small(s, (unsigned char*)&ms, q, p, total);
   while (n > 1 || (n == 1 && q.d[0].scale != 1)) {
     const uint32_t h = n > 1 ? n >> 1 : 1;
     for (uint32_t i = 0; i < h; ++i) {
