@@ -1256,7 +1256,9 @@ struct MergeSmem {
   uint32_t warp_sum[WARPS_PER_BLOCK];
   uint32_t split_a, split_b;
 };
-constexpr size_t RED_SMEM_BYTES = (size_t)WARPS_PER_BLOCK * SORT_TILE * 12;  // the warps' sort tiles
+// the warps' sort tiles, or the block's merge and generation staging area
+constexpr size_t RED_SMEM_BYTES = 40 * 1024;
+static_assert((size_t)WARPS_PER_BLOCK * SORT_TILE * 12 <= RED_SMEM_BYTES, "sort tiles fit");
 static_assert(sizeof(MergeSmem) <= RED_SMEM_BYTES, "merge tile overlays the sort tiles");
 static_assert(2 * WARPS_PER_BLOCK * 32 * 24 <= RED_SMEM_BYTES, "small merge fits the sort tiles");
 
@@ -1275,6 +1277,7 @@ struct MergeReq {
   uint64_t gidx;  // simplex whose coboundary is to be generated
   uint32_t grank;
   uint32_t wsum[WARPS_PER_BLOCK];
+  uint32_t roff[33];  // run offsets of a merge staged in shared memory
   unsigned long long off;
   uint32_t take;  // the heavy column this block takes next
 };
@@ -1504,7 +1507,8 @@ __device__ uint32_t block_axpy(MergeSmem& ms, const RunDesc& A, const RunDesc& B
 // The runs of a merge request, summed two at a time (a tree of block_axpy)
 // into q.d[0] with scale 1.  Called by the whole block; false (in every
 // thread) when the arena is full.
-constexpr uint32_t SMALL_MERGE = 2 * WARPS_PER_BLOCK * 32;  // entries merged in one shared-memory pass
+constexpr uint32_t SMALL_MERGE = 2 * WARPS_PER_BLOCK * 32;  // capacity of the rank-count merge
+constexpr uint32_t SMALL_MERGE_USE = 128;  // it counts ranks in O(total^2): used up to this size only
 
 // The request's runs when they hold at most SMALL_MERGE entries together: all
 // entries are loaded into shared memory at once, each is placed by its rank
@@ -1578,12 +1582,186 @@ __device__ bool block_merge_small(const RedState& s, unsigned char* raw, MergeRe
   return true;
 }
 
+constexpr uint32_t MID_MERGE = (uint32_t)(RED_SMEM_BYTES / 12);  // entries staged in shared memory at once
+
+// first position in the sorted keys k[0, len) whose key is >= x
+__device__ __forceinline__ uint32_t lower_bound_u64(const uint64_t* k, uint32_t len, uint64_t x) {
+  uint32_t lo = 0, hi = len;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (k[mid] < x) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Merge the ranges [lo[r], hi[r]) of the request's runs (shared-memory arrays;
+// at most MID_MERGE entries together) and append the nonzero sums to (fk, fc)
+// from position `out`; returns how many were appended (the same in every
+// thread).  All keys and scaled coefficients of the ranges are staged in shared
+// memory; every entry finds its place in the merged order by binary searches in
+// the other ranges (equal keys ordered by run); the entry of the first run
+// holding a key takes the group's coefficient sum, the others coefficient 0;
+// that order goes to the scratch (tk, tc), from which a block scan packs the
+// nonzero entries.  Called by the whole block.
+__device__ uint32_t chunk_merge(MergeReq& q, unsigned char* raw, const uint32_t* lo, const uint32_t* hi, uint32_t n,
+                                uint32_t p, uint64_t* tk, uint32_t* tc, uint64_t* fk, uint32_t* fc, uint32_t out) {
+  const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  uint64_t* sk = (uint64_t*)raw;
+  uint32_t* sc = (uint32_t*)(raw + (size_t)MID_MERGE * 8);
+  if (tid == 0) {
+    uint32_t acc = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+      q.roff[i] = acc;
+      acc += hi[i] - lo[i];
+    }
+    q.roff[n] = acc;
+  }
+  __syncthreads();
+  const uint32_t total = q.roff[n];
+  for (uint32_t e = tid; e < total; e += blockDim.x) {
+    uint32_t r = 0;
+    while (e >= q.roff[r + 1]) ++r;
+    const RunDesc& R = q.d[r];
+    const uint32_t i = lo[r] + e - q.roff[r];
+    sk[e] = R.key[i];
+    sc[e] = R.scale == 1 ? R.coef[i] : (uint32_t)(((uint64_t)R.coef[i] * R.scale) % p);
+  }
+  __syncthreads();
+  for (uint32_t e = tid; e < total; e += blockDim.x) {
+    uint32_t r = 0;
+    while (e >= q.roff[r + 1]) ++r;
+    const uint64_t k = sk[e];
+    uint32_t pos = e - q.roff[r], c = sc[e];
+    bool head = true;
+    for (uint32_t r2 = 0; r2 < n; ++r2) {
+      if (r2 == r) continue;
+      const uint32_t b = q.roff[r2], len = q.roff[r2 + 1] - b;
+      const uint32_t lb = lower_bound_u64(sk + b, len, k);
+      const bool eq = lb < len && sk[b + lb] == k;
+      if (r2 < r) {
+        pos += lb + (eq ? 1u : 0u);
+        head = head && !eq;
+      } else {
+        pos += lb;
+        if (eq) c = (c + sc[b + lb]) % p;
+      }
+    }
+    tk[pos] = k;
+    tc[pos] = head ? c : 0u;
+  }
+  __syncthreads();
+  // pack: thread t takes the entries [t * per, (t + 1) * per) of the merged order
+  const uint32_t per = (total + blockDim.x - 1) / blockDim.x;
+  const uint32_t e0 = tid * per < total ? tid * per : total;
+  const uint32_t e1 = e0 + per < total ? e0 + per : total;
+  uint32_t cnt = 0;
+  for (uint32_t e = e0; e < e1; ++e) cnt += tc[e] != 0;
+  uint32_t incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= (uint32_t)o) incl += t;
+  }
+  if (lane == 31) q.wsum[wid] = incl;
+  __syncthreads();
+  uint32_t base = 0, kept = 0;
+  for (uint32_t w = 0; w < WARPS_PER_BLOCK; ++w) {
+    if (w < wid) base += q.wsum[w];
+    kept += q.wsum[w];
+  }
+  uint32_t o = out + base + incl - cnt;
+  for (uint32_t e = e0; e < e1; ++e) {
+    if (tc[e]) {
+      fk[o] = tk[e];
+      fc[o] = tc[e];
+      ++o;
+    }
+  }
+  __syncthreads();  // the staging area, offsets and sums are reused
+  return kept;
+}
+
+constexpr uint32_t MERGE_CHUNKS = 256;  // most chunks of one big merge
+
+// The request's runs merged in one pass into one run of scale 1 in q.d[0], in
+// chunks of at most MID_MERGE entries: splitters taken every S entries of the
+// longest run cut every run into consecutive ranges (one round of binary
+// searches, in parallel), and chunk_merge merges the ranges chunk after chunk
+// onto the end of the output.  Returns 0 (in every thread) when the arena is
+// full, -1 when the runs are too unevenly spread for chunks of that size (the
+// caller then merges two runs at a time), 1 on success.
+__device__ int block_merge_chunked(const RedState& s, unsigned char* raw, MergeReq& q, uint32_t p, uint32_t total) {
+  const uint32_t tid = threadIdx.x;
+  const uint32_t n = q.n;
+  uint32_t L = 0;
+  for (uint32_t i = 1; i < n; ++i)
+    if (q.d[i].len > q.d[L].len) L = i;
+  const uint32_t lenL = q.d[L].len;
+  // S entries of the longest run per chunk, so a chunk holds about n * S when the runs are alike
+  uint32_t S = MID_MERGE / (2 * n);
+  if (S < 16) S = 16;
+  uint32_t K = total <= MID_MERGE ? 1u : (lenL + S - 1) / S;
+  if (K < 1) K = 1;
+  if (K > MERGE_CHUNKS) return -1;
+  // arena: scratch for one chunk, the output, and the chunk boundaries
+  const unsigned long long want = (unsigned long long)MID_MERGE + total + (unsigned long long)K * n;
+  if (tid == 0) q.off = atomicAdd(s.r_top, want);
+  __syncthreads();
+  const unsigned long long off = q.off;
+  if (off + want > s.r_cap) return 0;
+  // bnd[c * n + r] = where run r enters chunk c + 1
+  uint32_t* bnd = s.r_coef + off + MID_MERGE + total;
+  for (uint32_t t = tid; t < (K - 1) * n; t += blockDim.x) {
+    const uint32_t c = t / n, r = t % n;
+    const uint64_t sp = q.d[L].key[(c + 1) * S];
+    bnd[t] = r == L ? (c + 1) * S : lower_bound_u64(q.d[r].key, q.d[r].len, sp);
+  }
+  __shared__ int fits;
+  if (tid == 0) fits = 1;
+  __syncthreads();
+  for (uint32_t c = tid; c < K; c += blockDim.x) {
+    uint32_t sz = 0;
+    for (uint32_t r = 0; r < n; ++r) {
+      const uint32_t a0 = c ? bnd[(c - 1) * n + r] : 0u, a1 = c + 1 < K ? bnd[c * n + r] : q.d[r].len;
+      sz += a1 - a0;
+    }
+    if (sz > MID_MERGE) fits = 0;
+  }
+  __syncthreads();
+  if (!fits) return -1;
+  uint64_t* tk = s.r_key + off;
+  uint32_t* tc = s.r_coef + off;
+  uint64_t* fk = s.r_key + off + MID_MERGE;
+  uint32_t* fc = s.r_coef + off + MID_MERGE;
+  __shared__ uint32_t clo[32], chi[32];
+  uint32_t out = 0;
+  for (uint32_t c = 0; c < K; ++c) {
+    if (tid < n) {
+      clo[tid] = c ? bnd[(c - 1) * n + tid] : 0u;
+      chi[tid] = c + 1 < K ? bnd[c * n + tid] : q.d[tid].len;
+    }
+    __syncthreads();
+    out += chunk_merge(q, raw, clo, chi, n, p, tk, tc, fk, fc, out);
+  }
+  if (tid == 0) {
+    q.d[0] = RunDesc{fk, fc, out, 1};
+    atomicAdd(s.compacted, (unsigned long long)total);
+  }
+  __syncthreads();
+  return 1;
+}
+
 __device__ bool block_merge_runs(const RedState& s, MergeSmem& ms, MergeReq& q, uint32_t p) {
   const RunDesc none{nullptr, nullptr, 0, 1};
   uint32_t n = q.n;
   uint32_t total = 0;
   for (uint32_t i = 0; i < n; ++i) total += q.d[i].len;
-  if (total <= SMALL_MERGE) return block_merge_small(s, (unsigned char*)&ms, q, p, total);
+  if (total <= SMALL_MERGE_USE) return block_merge_small(s, (unsigned char*)&ms, q, p, total);
+  {
+    const int r = block_merge_chunked(s, (unsigned char*)&ms, q, p, total);
+    if (r >= 0) return r == 1;
+  }
   while (n > 1 || (n == 1 && q.d[0].scale != 1)) {
     const uint32_t h = n > 1 ? n >> 1 : 1;
     for (uint32_t i = 0; i < h; ++i) {
