@@ -244,6 +244,26 @@ RIPS_API int rips_get_tuning(int32_t dim, int64_t n, rips_tuning_t* out);
 /* Forget every entry (back to the built-in defaults). */
 RIPS_API void rips_clear_tuning(void);
 
+/* Bounds of the library's waits and first buffer sizes.  The paper has no
+ * counterpart.  Every device wait is bounded: a block waiting at the
+ * reduction's grid barrier gives up (and the call returns
+ * RIPS_ERR_DEVICE_TIMEOUT) when no block has made progress for barrier_wait_ns,
+ * and one column's chain of additions gives up after chain_ns.  Setting them
+ * small, or the arena and pivot table tiny, injects the failures the library
+ * must report cleanly (a timeout status, an arena that is grown and the
+ * dimension redone, RIPS_ERR_OOM for a full table) without faulting or hanging
+ * the GPU; the defaults (all fields 0) never trigger them in normal use. */
+typedef struct rips_limits {
+  uint64_t barrier_wait_ns; /* 0: 30 s */
+  uint64_t chain_ns;        /* 0: 600 s */
+  uint64_t arena_entries;   /* first reduction-arena size in entries (0: from the column count) */
+  uint64_t table_slots;     /* pivot-table capacity, a power of two (0: 2 x columns, rounded up) */
+} rips_limits_t;
+
+/* Process-wide; RIPS_ERR_BAD_ARG if table_slots is not 0 or a power of two. */
+RIPS_API int rips_set_limits(const rips_limits_t* limits);
+RIPS_API int rips_get_limits(rips_limits_t* out);
+
 #ifdef __cplusplus
 }
 #endif

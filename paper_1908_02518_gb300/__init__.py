@@ -184,6 +184,19 @@ def backward(result: Result, points, grad_birth, grad_death, grad_dist=None, str
     return g
 
 
+def set_limits(barrier_wait_ns: int = 0, chain_ns: int = 0, arena_entries: int = 0, table_slots: int = 0) -> None:
+    """Bounds of the device waits and first buffer sizes (0 = default); small
+    values inject the failures the library reports as status codes."""
+    lim = _lib.Limits(barrier_wait_ns, chain_ns, arena_entries, table_slots)
+    _lib.check(_lib.load().rips_set_limits(C.byref(lim)), "rips_set_limits")
+
+
+def get_limits() -> dict:
+    lim = _lib.Limits()
+    _lib.check(_lib.load().rips_get_limits(C.byref(lim)), "rips_get_limits")
+    return {f: int(getattr(lim, f)) for f, _ in _lib.Limits._fields_}
+
+
 def launch_count(reset: bool = False) -> int:
     return int(_lib.load().rips_kernel_launch_count(1 if reset else 0))
 

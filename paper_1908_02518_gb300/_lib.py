@@ -29,6 +29,11 @@ class Stats(C.Structure):
                 ("compacted_entries", C.c_int64), ("added_entries", C.c_int64)]
 
 
+class Limits(C.Structure):
+    _fields_ = [("barrier_wait_ns", C.c_uint64), ("chain_ns", C.c_uint64), ("arena_entries", C.c_uint64),
+                ("table_slots", C.c_uint64)]
+
+
 class Tuning(C.Structure):
     _fields_ = [("warp_chain_limit", C.c_int32), ("warp_merge_max", C.c_int32),
                 ("reduce_blocks_per_sm", C.c_int32), ("scan_blocks_per_sm", C.c_int32)]
@@ -41,6 +46,7 @@ EXPORTS = [
     "rips_result_dim_max", "rips_result_threshold", "rips_result_stats", "rips_result_phase_ms",
     "rips_result_free", "rips_status_string", "rips_kernel_launch_count", "rips_set_kernel_timing",
     "rips_result_kernel_ms", "rips_h0_barcode_noalloc", "rips_set_tuning", "rips_get_tuning", "rips_clear_tuning",
+    "rips_set_limits", "rips_get_limits",
 ]
 
 KERNEL_CLASSES = ["prologue", "edge_sort", "h0", "enumerate", "apparent", "col_sort", "pivot_init", "reduce",
@@ -105,6 +111,10 @@ def load(build_if_missing: bool = True):
     lib.rips_get_tuning.restype = C.c_int
     lib.rips_clear_tuning.argtypes = []
     lib.rips_clear_tuning.restype = None
+    lib.rips_set_limits.argtypes = [C.POINTER(Limits)]
+    lib.rips_set_limits.restype = C.c_int
+    lib.rips_get_limits.argtypes = [C.POINTER(Limits)]
+    lib.rips_get_limits.restype = C.c_int
     _lib = lib
     return lib
 

@@ -199,6 +199,14 @@ std::mutex g_tune_mu;
 std::vector<TuneEntry> g_tune;
 constexpr rips_tuning_t TUNE_DEFAULT{32, 2048, 0, 16};
 
+std::mutex g_limits_mu;
+rips_limits_t g_limits{0, 0, 0, 0};
+
+rips_limits_t current_limits() {
+  std::lock_guard<std::mutex> g(g_limits_mu);
+  return g_limits;
+}
+
 rips_tuning_t tuning_for(int dim, int64_t n) {
   std::lock_guard<std::mutex> g(g_tune_mu);
   for (auto it = g_tune.rbegin(); it != g_tune.rend(); ++it)
@@ -252,7 +260,8 @@ int check_args(int64_t n, int32_t dim_max, float threshold, uint32_t p) {
 int map_device_error(uint32_t e) {
   if (e & ERRF_BAD_INPUT) return RIPS_ERR_BAD_ARG;
   if (e & ERRF_TIMEOUT) return RIPS_ERR_DEVICE_TIMEOUT;
-  if (e & (ERRF_INTERNAL | ERRF_TABLE_FULL)) return RIPS_ERR_INTERNAL;
+  if (e & ERRF_TABLE_FULL) return RIPS_ERR_OOM;  // the cause; lookups that then miss also flag INTERNAL
+  if (e & ERRF_INTERNAL) return RIPS_ERR_INTERNAL;
   return RIPS_OK;
 }
 
@@ -560,7 +569,8 @@ int run_batch(Workspace& w, const float* dD, const std::vector<int64_t>& ns, int
 
     // reduction
     const int tb = cur;  // table for this dimension (the other one holds d-1)
-    const uint32_t tcap = pow2_at_least(2ull * M + 16);
+    const rips_limits_t lim = current_limits();
+    const uint32_t tcap = lim.table_slots ? (uint32_t)lim.table_slots : pow2_at_least(2ull * M + 16);
     CR(ensure(w.tkeys[tb], (size_t)tcap * 8));
     CR(ensure(w.tvals[tb], (size_t)tcap * 4));
     CR(ensure(w.piv_key, (size_t)(M + 1) * 8));
@@ -578,7 +588,8 @@ int run_batch(Workspace& w, const float* dD, const std::vector<int64_t>& ns, int
     if (blocks < 1) return RIPS_ERR_CUDA;
     uint32_t slice = 32;
     while (slice < max_deg + 1) slice <<= 1;
-    size_t rcap = std::max<size_t>(w.r_cap, std::max<size_t>(16 * (size_t)M, (size_t)1 << 22));
+    size_t rcap = lim.arena_entries ? (size_t)lim.arena_entries
+                                    : std::max<size_t>(w.r_cap, std::max<size_t>(16 * (size_t)M, (size_t)1 << 22));
     bool done = false;
     for (int attempt = 0; attempt < 6 && !done; ++attempt) {
       CR(ensure(w.r_key, rcap * 8));
@@ -613,6 +624,8 @@ int run_batch(Workspace& w, const float* dD, const std::vector<int64_t>& ns, int
       rs.max_chain = counts + 7;
       rs.heartbeat = counts + 12;
       rs.added = P<unsigned long long>(w.lists) + 7;
+      rs.barrier_ns = lim.barrier_wait_ns ? lim.barrier_wait_ns : 30ull * 1000 * 1000 * 1000;
+      rs.chain_ns = lim.chain_ns ? lim.chain_ns : 600ull * 1000 * 1000 * 1000;
       rs.err = P<uint32_t>(w.err);
       {
         KTimer kt(w, RIPS_K_REDUCE, s);
@@ -1001,6 +1014,22 @@ RIPS_API int rips_get_tuning(int32_t dim, int64_t n, rips_tuning_t* out) {
 RIPS_API void rips_clear_tuning(void) {
   std::lock_guard<std::mutex> g(g_tune_mu);
   g_tune.clear();
+}
+
+RIPS_API int rips_set_limits(const rips_limits_t* limits) {
+  if (!limits) return RIPS_ERR_BAD_ARG;
+  const uint64_t t = limits->table_slots;
+  if (t && (t & (t - 1))) return RIPS_ERR_BAD_ARG;
+  if (t > (1ull << 31)) return RIPS_ERR_BAD_ARG;
+  std::lock_guard<std::mutex> g(g_limits_mu);
+  g_limits = *limits;
+  return RIPS_OK;
+}
+
+RIPS_API int rips_get_limits(rips_limits_t* out) {
+  if (!out) return RIPS_ERR_BAD_ARG;
+  *out = current_limits();
+  return RIPS_OK;
 }
 
 RIPS_API int rips_barcodes_batched(const float* d_points, const int64_t* offsets, int32_t batch, int32_t k,

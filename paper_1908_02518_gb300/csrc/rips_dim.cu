@@ -59,7 +59,6 @@ namespace {
 
 constexpr int WARPS_PER_BLOCK = 8;
 constexpr uint32_t MAX_PIVOT_PASSES = 1u << 30;  // additions in one chain before giving up
-constexpr unsigned long long CHAIN_LIMIT_NS = 600ull * 1000 * 1000 * 1000;  // or 10 min in one chain
 constexpr uint8_t HEAVY = 2;                      // flag in RedState::reduced: reduced block-wide
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -989,7 +988,7 @@ __device__ int chain_advance(const DimArgs& a, const RedState& s, const CV& cv, 
     if ((ch.step & 255) == 255) {  // the chain's wall-clock bound
       const unsigned long long now = __shfl_sync(0xffffffffu, global_ns(), 0);
       if (ch.t0 == 0) ch.t0 = now;
-      else if (now - ch.t0 > CHAIN_LIMIT_NS) return CH_LONG;
+      else if (now - ch.t0 > s.chain_ns) return CH_LONG;
     }
     if (block && !ch.started) {
       const uint32_t jn = s.r_len[j];
@@ -1876,14 +1875,14 @@ __device__ void reduce_one_block(const DimArgs& a, const RedState& s, const Bino
   chain_finish(s, ch, lane, j, claim_count);
 }
 
-constexpr unsigned long long BARRIER_LIMIT_NS = 30ull * 1000 * 1000 * 1000;  // 30 s
 
 // Grid-wide barrier for a cooperative launch (all blocks co-resident).  The
-// wait is bounded: when BARRIER_LIMIT_NS pass with no block making progress
+// wait is bounded: when limit_ns pass with no block making progress
 // (the heartbeat counter, bumped by long chains of additions, stands still) the
 // block records ERRF_TIMEOUT and returns false, and the caller leaves the
 // kernel.
-__device__ bool grid_barrier(unsigned* count, unsigned* gen, const unsigned* heartbeat, uint32_t* err) {
+__device__ bool grid_barrier(unsigned* count, unsigned* gen, const unsigned* heartbeat, unsigned long long limit_ns,
+                             uint32_t* err) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -1900,7 +1899,7 @@ __device__ bool grid_barrier(unsigned* count, unsigned* gen, const unsigned* hea
       while (*(volatile unsigned*)gen == g) {
         __nanosleep(128);
         const unsigned long long now = global_ns();
-        if (now - t0 > BARRIER_LIMIT_NS) {
+        if (now - t0 > limit_ns) {
           const unsigned h = *(volatile const unsigned*)heartbeat;
           if (h != hb) {  // another block is still working
             hb = h;
@@ -1956,7 +1955,7 @@ __global__ void __launch_bounds__(256, 2) reduce_persistent_kernel(DimArgs a, Re
 
   for (uint32_t j = warp_id; j < s.ncols; j += warps)
     init_column(a, s, B, lane, tile, j, &claim_cnt[0], &heavy_cnt[0], heavy[0]);
-  if (!grid_barrier(bar_count, bar_gen, s.heartbeat, a.err)) return;
+  if (!grid_barrier(bar_count, bar_gen, s.heartbeat, s.barrier_ns, a.err)) return;
   uint32_t r = 0;
   for (;; ++r) {
     const int src = r & 1, dst = src ^ 1;
@@ -1972,7 +1971,7 @@ __global__ void __launch_bounds__(256, 2) reduce_persistent_kernel(DimArgs a, Re
       *light_next = 0;
       *heavy_next = 0;
     }
-    if (!grid_barrier(bar_count, bar_gen, s.heartbeat, a.err)) return;
+    if (!grid_barrier(bar_count, bar_gen, s.heartbeat, s.barrier_ns, a.err)) return;
     if (tid == 0) {
       claim_cnt[src] = 0;
       red_cnt[dst] = 0;
@@ -2001,7 +2000,7 @@ __global__ void __launch_bounds__(256, 2) reduce_persistent_kernel(DimArgs a, Re
         reduce_one(a, s, B, lane, tile, s.reduce_list[t], &claim_cnt[dst], &heavy_cnt[dst], heavy[dst]);
       }
     }
-    if (!grid_barrier(bar_count, bar_gen, s.heartbeat, a.err)) return;
+    if (!grid_barrier(bar_count, bar_gen, s.heartbeat, s.barrier_ns, a.err)) return;
   }
   if (tid == 0) ctl[6] = r;
 }

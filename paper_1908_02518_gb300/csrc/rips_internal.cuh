@@ -26,7 +26,7 @@ constexpr int MAX_DIM = 8;  // largest simplex dimension handled (vertices per s
 // device error flag bits (written with atomicOr into Workspace::d_err)
 enum : uint32_t {
   ERRF_TIMEOUT = 1u,       // a bounded loop hit its limit
-  ERRF_TABLE_FULL = 2u,    // pivot hash table probe limit reached
+  ERRF_TABLE_FULL = 2u,    // a hash table is full
   ERRF_INTERNAL = 4u,      // consistency check failed
   ERRF_ARENA = 8u,         // V arena exhausted (retry after growth)
   ERRF_BAD_INPUT = 16u,    // NaN / negative / infinite distance
@@ -216,6 +216,8 @@ struct RedState {
   uint32_t* max_chain;            // longest chain of additions (profiling)
   unsigned* heartbeat;            // bumped while chains of additions make progress
   unsigned long long* added;      // entries of the columns added (profiling)
+  unsigned long long barrier_ns;  // grid-barrier wait without progress before giving up
+  unsigned long long chain_ns;    // one chain of additions before giving up
   uint32_t* err;
 };
 

@@ -62,3 +62,16 @@ def test_save_and_load_round_trip(tmp_path):
     tuning.clear_tuning()
     tuning.load(path)
     assert tuning.get_tuning(1, 300)["warp_chain_limit"] == 8
+
+
+def test_limits_round_trip_and_validation():
+    import paper_1908_02518_gb300 as rg
+    try:
+        rg.set_limits(barrier_wait_ns=5, chain_ns=6, arena_entries=7, table_slots=64)
+        assert rg.get_limits() == {"barrier_wait_ns": 5, "chain_ns": 6, "arena_entries": 7, "table_slots": 64}
+        for bad in (3, 100, 1 << 40):
+            with pytest.raises(_lib.RipsError):
+                rg.set_limits(table_slots=bad)
+    finally:
+        rg.set_limits()
+    assert rg.get_limits() == {"barrier_wait_ns": 0, "chain_ns": 0, "arena_entries": 0, "table_slots": 0}
