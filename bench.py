@@ -226,6 +226,19 @@ def run_batched(args):
         step(pts, offsets)
     t_batch, (gx, loss, units) = timed(lambda: step(pts, offsets), max(args.steps // 4, 3))
 
+    # the same forward as one CUDA-graph replay of a batch plan (sizes fixed in advance)
+    plan = rg.BatchPlan(offsets, pts.shape[1])
+    graph = plan.capture(pts)
+
+    def replay():
+        graph.replay()
+        return plan.result()
+    t_graph_fwd, gres = timed(replay, max(args.steps // 4, 3))
+    t_fwd, fres = timed(lambda: rg.barcodes_batched(pts, offsets, 1), max(args.steps // 4, 3))
+    graph_same = sorted(map(tuple, gres.bars[["cloud", "dim", "birth", "death"]].tolist())) == \
+        sorted(map(tuple, fres.bars[["cloud", "dim", "birth", "death"]].tolist()))
+    plan.free()
+
     def loop():
         gs, ls, us = [], 0.0, 0
         for x in dev_clouds:
@@ -246,7 +259,9 @@ def run_batched(args):
         return 0
     print(json.dumps({"metric": "batched_forward_backward_ms", "value": t_batch_job, "unit": "ms",
                       "higher_is_better": False, "n_gpus": world, "per_cloud_loop_ms": t_loop_job,
-                      "speedup": t_loop_job / t_batch_job, "clouds_on_rank0": len(clouds),
+                      "speedup": t_loop_job / t_batch_job, "forward_ms": max_over_ranks(t_fwd),
+                      "forward_graph_replay_ms": max_over_ranks(t_graph_fwd), "graph_bars_equal": graph_same,
+                      "clouds_on_rank0": len(clouds),
                       "points_on_rank0": int(offsets[-1]), "simplices": units_job,
                       "simplices_per_s": whole_job_rate(units_job, t_batch_job), "loss_rank0": loss,
                       "loss_close_to_loop": math.isclose(loss, loss_l, rel_tol=1e-9), "grad_max_rel_diff_to_loop": gdiff / gscale,

@@ -264,6 +264,29 @@ typedef struct rips_limits {
 RIPS_API int rips_set_limits(const rips_limits_t* limits);
 RIPS_API int rips_get_limits(rips_limits_t* out);
 
+/* Batch plans (the batched problem of rips_barcodes_batched for barcodes H0 and
+ * H1, with every launch fixed in advance).  A plan is made once for a list of
+ * cloud sizes (`offsets`, batch + 1 point offsets as in rips_barcodes_batched),
+ * k coordinates, a threshold and p; it allocates every buffer for the worst
+ * case (all C(n, 2) edges of every cloud), at most 12800 points per cloud.
+ * rips_batch_plan_run enqueues the whole forward for new point coordinates
+ * (same sizes) on the caller's stream without any host synchronisation or
+ * allocation, so it may be captured into a CUDA graph and replayed;
+ * rips_batch_plan_result waits for the stream and returns the last run's bars
+ * and statistics as a result (for the accessors and rips_barcodes_backward).
+ * The reduction's arena is fixed too: arena_entries entries of 12 bytes (0:
+ * 384 per edge, within 40 % of the free device memory; the arena keeps every
+ * intermediate run of a reduction, 150 to 250 entries per edge on the 256-cloud
+ * mix of circles, tori and cubes); a run that needs more
+ * reports RIPS_ERR_OOM from rips_batch_plan_result.  A plan is used by one
+ * stream at a time. */
+typedef struct rips_batch_plan rips_batch_plan_t;
+RIPS_API int rips_batch_plan_create(const int64_t* offsets, int32_t batch, int32_t k, float threshold, uint32_t p,
+                                    int64_t arena_entries, rips_batch_plan_t** out);
+RIPS_API int rips_batch_plan_run(rips_batch_plan_t* plan, const float* d_points, void* cuda_stream);
+RIPS_API int rips_batch_plan_result(rips_batch_plan_t* plan, void* cuda_stream, rips_result_t** out);
+RIPS_API void rips_batch_plan_free(rips_batch_plan_t* plan);
+
 #ifdef __cplusplus
 }
 #endif

@@ -197,6 +197,63 @@ def get_limits() -> dict:
     return {f: int(getattr(lim, f)) for f, _ in _lib.Limits._fields_}
 
 
+class BatchPlan:
+    """Barcodes H0 and H1 of batches of clouds with fixed sizes, every launch
+    fixed in advance (``rips_batch_plan_*``): ``run`` enqueues the whole forward
+    for new coordinates without host synchronisation or allocation, so it can
+    be captured into a CUDA graph (``capture``) and replayed; ``result`` waits
+    for the stream and returns the last run's bars."""
+
+    def __init__(self, offsets, k: int, threshold: float = math.inf, p: int = 2, arena_entries: int = 0):
+        self._lib = _lib.load()
+        self._off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        self.k = k
+        h = C.c_void_p()
+        _lib.check(self._lib.rips_batch_plan_create(self._off.ctypes.data_as(C.POINTER(C.c_int64)), len(self._off) - 1,
+                                                    k, C.c_float(threshold), p, arena_entries, C.byref(h)),
+                   "rips_batch_plan_create")
+        self._h = h
+
+    def run(self, points, stream=None) -> None:
+        import torch
+        if not points.is_cuda or points.dtype != torch.float32 or not points.is_contiguous():
+            raise ValueError("points must be a contiguous float32 CUDA tensor")
+        _lib.check(self._lib.rips_batch_plan_run(self._h, C.c_void_p(points.data_ptr()), _stream_ptr(stream)),
+                   "rips_batch_plan_run")
+
+    def result(self, stream=None, keep_handle: bool = False) -> Result:
+        out = C.c_void_p()
+        _lib.check(self._lib.rips_batch_plan_result(self._h, _stream_ptr(stream), C.byref(out)),
+                   "rips_batch_plan_result")
+        return _collect(self._lib, out, keep_handle)
+
+    def capture(self, points):
+        """A CUDA graph of ``run(points)``; replay it after writing new
+        coordinates into ``points`` (same tensor), then call ``result``."""
+        import torch
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):  # a first run outside the capture (kernel attributes set, memory touched)
+            self.run(points, side)
+            self.result(side)
+        torch.cuda.current_stream().wait_stream(side)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, capture_error_mode="relaxed"):
+            self.run(points, torch.cuda.current_stream())
+        return g
+
+    def free(self) -> None:
+        if getattr(self, "_h", None):
+            self._lib.rips_batch_plan_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
 def launch_count(reset: bool = False) -> int:
     return int(_lib.load().rips_kernel_launch_count(1 if reset else 0))
 

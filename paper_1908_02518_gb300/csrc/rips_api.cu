@@ -619,6 +619,7 @@ int run_batch(Workspace& w, const float* dD, const std::vector<int64_t>& ns, int
       rs.claim_list = P<uint32_t>(w.claim);
       rs.reduce_list = P<uint32_t>(w.reduce);
       rs.heavy_list = P<uint32_t>(w.heavy);
+      rs.ncols_dev = nullptr;
       rs.steps = P<unsigned long long>(w.lists) + 4;
       rs.compacted = P<unsigned long long>(w.lists) + 5;
       rs.max_chain = counts + 7;
@@ -871,6 +872,364 @@ int backward_locked(Workspace& w, const rips_result* r, const float* d_points, i
   return RIPS_OK;
 }
 
+
+// ------------------------------------------------------------------ batch plans
+// A batch plan fixes the clouds' sizes (and k, threshold, p; dimensions 0 and
+// 1) and sizes every buffer from the worst case at creation: all C(n, 2)
+// edges of every cloud, all of them columns.  Lists then have a fixed
+// capacity, the parts past their device-side counts are padded with the
+// largest key (sorted last, skipped by the kernels), and nothing between two
+// kernels needs a count on the host.  plan_run therefore only enqueues device
+// work and can be captured into a CUDA graph; plan_result reads everything back
+// afterwards.
+struct PlanState {
+  Workspace w;
+  int32_t C = 0, k = 0;
+  float threshold = 0.0f;
+  uint32_t p = 2;
+  int n_max = 1;
+  std::vector<int64_t> ns, offsets;
+  uint64_t N = 0, RR = 0, e_cap = 0, drows = 0, vtiles = 0;
+  int eb = 0, cb = 0;
+  DimArgs a{};
+  uint32_t tcap = 0;
+  uint64_t acap = 0;
+  size_t arena = 0;
+  int blocks = 0;
+  uint32_t slice = 0;
+  Buf clouds0, dtile;
+};
+
+constexpr int PLAN_SPC = 32;  // statistics counters per cloud (dimensions 0 and 1)
+
+void release(Buf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+}
+
+void release_plan(PlanState& pl) {
+  Workspace& w = pl.w;
+  Buf* all[] = {&w.dist, &w.binom, &w.rowmax, &w.teff, &w.err, &w.ecount, &w.ekeys, &w.ekeys_alt, &w.eflags,
+                &w.escan, &w.erank, &w.rvalue, &w.R, &w.deg, &w.nbr, &w.eu, &w.ev, &w.comp, &w.best, &w.parent,
+                &w.gtop, &w.inforest, &w.fpos, &w.nf, &w.sidx[0], &w.sidx[1], &w.srank[0], &w.srank[1],
+                &w.scount, &w.ckeys, &w.ckeys_alt, &w.ccount, &w.sorttmp, &w.piv_key, &w.piv_coef, &w.r_off,
+                &w.r_len, &w.reduced, &w.claim, &w.reduce, &w.heavy, &w.lists, &w.r_key, &w.r_coef, &w.r_top,
+                &w.tkeys[0], &w.tkeys[1], &w.tvals[0], &w.tvals[1], &w.amk[0], &w.amk[1], &w.amv[0], &w.amv[1],
+                &w.bars, &w.bars_alt, &w.bk0, &w.bk1, &w.bp0, &w.bp1, &w.bartmp, &w.nbars, &w.stats,
+                &w.bwd_bars, &w.bwd_off, &w.cdist, &w.clouds, &w.tileoff, &w.vcloud, &w.ccounts, &pl.clouds0,
+                &pl.dtile};
+  for (Buf* b : all) release(*b);
+}
+
+int plan_create(PlanState& pl, const int64_t* offsets, int32_t batch, int32_t k, float threshold, uint32_t p,
+                int64_t arena_entries) {
+  if (!offsets || batch < 1 || k < 1 || offsets[0] < 0 || arena_entries < 0) return RIPS_ERR_BAD_ARG;
+  if (!is_prime(p) || p >= 65536) return RIPS_ERR_BAD_MODULUS;
+  if (!std::isnan(threshold) && threshold < 0.0f) return RIPS_ERR_BAD_ARG;
+  pl.C = batch;
+  pl.k = k;
+  pl.threshold = threshold;
+  pl.p = p;
+  pl.offsets.assign(offsets, offsets + batch + 1);
+  pl.ns.resize(batch);
+  std::vector<CloudInfo> ci(batch);
+  std::vector<uint32_t> dtile(batch + 1), vtile(batch + 1);
+  for (int32_t c = 0; c < batch; ++c) {
+    const int64_t n = offsets[c + 1] - offsets[c];
+    if (n < 1 || n > 46340) return RIPS_ERR_BAD_ARG;
+    pl.ns[c] = n;
+    pl.n_max = std::max<int>(pl.n_max, (int)n);
+    ci[c] = CloudInfo{(int)n, (uint32_t)(offsets[c] - offsets[0]), pl.RR, 0, 0, 0.0f, 0};
+    dtile[c] = (uint32_t)pl.drows;
+    vtile[c] = (uint32_t)pl.vtiles;
+    const uint64_t nb = ((uint64_t)n + 31) / 32;
+    pl.N += (uint64_t)n;
+    pl.RR += (uint64_t)n * (uint64_t)n;
+    pl.e_cap += (uint64_t)n * (uint64_t)(n - 1) / 2;
+    pl.drows += ((uint64_t)n + 7) / 8;
+    pl.vtiles += nb * (nb + 1) / 2;
+  }
+  dtile[batch] = (uint32_t)pl.drows;
+  vtile[batch] = (uint32_t)pl.vtiles;
+  if (pl.e_cap == 0 || !h0_blocks_fit(pl.n_max)) return RIPS_ERR_BAD_ARG;
+  if (pl.N > 0xFFFFFFF0ull || pl.e_cap > 0x7FFFFFF0ull || pl.vtiles > 0x7FFFFFFFull || pl.drows > 0x7FFFFFFFull)
+    return RIPS_ERR_OVERFLOW;
+  pl.cb = batch > 1 ? bit_width64((uint64_t)batch - 1) : 0;
+  pl.eb = bits_of_count(host_binom((uint64_t)pl.n_max, 2));
+  if (pl.cb + 32 + pl.eb > 64) return RIPS_ERR_OVERFLOW;
+  const int kmax = 3;
+  DimArgs& a = pl.a;
+  a.d = 1;
+  a.nclouds = batch;
+  a.bn = pl.n_max;
+  a.kmax = kmax;
+  a.smem_binom = (size_t)(kmax + 1) * (pl.n_max + 1) * 8 <= 48 * 1024;
+  a.p = p;
+  a.col_bits = bits_of_count(host_binom((uint64_t)pl.n_max, 2));
+  a.row_bits = bits_of_count(host_binom((uint64_t)pl.n_max, 3));
+  a.rank_bits = bit_width64(pl.e_cap) + 1;  // every rank is below e_cap, the padding's included
+  a.rank_max = (uint32_t)pl.e_cap;
+  if (a.rank_bits + a.row_bits > 63 || pl.cb + a.rank_bits + a.col_bits > 64 || pl.cb + a.row_bits > 64)
+    return RIPS_ERR_OVERFLOW;
+  {
+    const rips_tuning_t tu = tuning_for(1, pl.n_max);
+    a.chain_limit = (uint32_t)tu.warp_chain_limit;
+    a.merge_max = (uint32_t)tu.warp_merge_max;
+    a.reduce_blocks_per_sm = tu.reduce_blocks_per_sm;
+    a.scan_blocks_per_sm = tu.scan_blocks_per_sm;
+  }
+  a.pmap_keys = nullptr;
+  a.pmap_mask = 0;
+  pl.tcap = pow2_at_least(2ull * pl.e_cap + 16);
+  pl.acap = pow2_at_least(2ull * pl.e_cap + 16);
+  if (arena_entries) {
+    pl.arena = (size_t)arena_entries;
+  } else {  // every merge and generated coboundary takes new arena space: 384 entries per edge, within 40 % of free memory
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+      cudaGetLastError();
+      free_b = (size_t)16 << 30;
+    }
+    pl.arena = std::max<size_t>(std::min<size_t>(384 * (size_t)pl.e_cap, free_b / 12 * 2 / 5), (size_t)1 << 22);
+  }
+  pl.slice = 32;
+  while (pl.slice < (uint32_t)pl.n_max + 1) pl.slice <<= 1;
+  Workspace& w = pl.w;
+  const uint64_t E = pl.e_cap, N = pl.N;
+  const size_t SPCB = (size_t)batch * PLAN_SPC * 8;
+  CR(ensure(w.clouds, (size_t)batch * sizeof(CloudInfo)));
+  CR(ensure(pl.clouds0, (size_t)batch * sizeof(CloudInfo)));
+  CR(ensure(pl.dtile, (size_t)(batch + 1) * 4));
+  CR(ensure(w.tileoff, (size_t)(batch + 1) * 4));
+  CR(ensure(w.vcloud, N * 4));
+  CR(ensure(w.ccounts, (size_t)(batch + 1) * 4));
+  CR(ensure(w.rowmax, N * 4));
+  CR(ensure(w.err, 16));
+  CR(ensure(w.ecount, 16));
+  CR(ensure(w.ekeys, E * 8));
+  CR(ensure(w.ekeys_alt, E * 8));
+  CR(ensure(w.sorttmp, std::max(sort_temp_bytes((uint32_t)E), scan_temp_bytes((uint32_t)std::max<uint64_t>(E, N + 1)))));
+  CR(ensure(w.eflags, (E + 1) * 4));
+  CR(ensure(w.erank, (E + 1) * 4));
+  CR(ensure(w.rvalue, (E + 1) * 4));
+  CR(ensure(w.R, pl.RR * 4));
+  CR(ensure(w.deg, (N + 2) * 4));
+  CR(ensure(w.nbr, 2 * E * 4));
+  CR(ensure(w.binom, (size_t)(kmax + 1) * (pl.n_max + 1) * 8));
+  CR(ensure(w.cdist, pl.RR * 4));
+  CR(ensure(w.bars, (N + E + 16) * sizeof(rips_bar_t)));
+  CR(ensure(w.eu, (E + 1) * 4));
+  CR(ensure(w.ev, (E + 1) * 4));
+  CR(ensure(w.inforest, E + 1));
+  CR(ensure(w.nbars, 16));
+  CR(ensure(w.stats, SPCB));
+  CR(ensure(w.sidx[0], (E + 1) * 8));
+  CR(ensure(w.srank[0], (E + 1) * 4));
+  CR(ensure(w.ckeys, (E + 1) * 8));
+  CR(ensure(w.ckeys_alt, (E + 1) * 8));
+  CR(ensure(w.ccount, 16));
+  CR(ensure(w.amk[0], pl.acap * 8));
+  CR(ensure(w.amv[0], pl.acap * 8));
+  CR(ensure(w.tkeys[0], (size_t)pl.tcap * 8));
+  CR(ensure(w.tvals[0], (size_t)pl.tcap * 4));
+  CR(ensure(w.piv_key, (E + 1) * 8));
+  CR(ensure(w.piv_coef, (E + 1) * 4));
+  CR(ensure(w.r_off, (E + 1) * 8));
+  CR(ensure(w.r_len, (E + 1) * 4));
+  CR(ensure(w.reduced, E + 1));
+  CR(ensure(w.claim, (E + 1) * 4));
+  CR(ensure(w.reduce, (E + 1) * 4));
+  CR(ensure(w.heavy, (E + 1) * 8));
+  CR(ensure(w.lists, 128));
+  CR(ensure(w.r_top, 16));
+  CR(ensure(w.r_key, pl.arena * 8));
+  CR(ensure(w.r_coef, pl.arena * 4));
+  w.r_cap = pl.arena;
+  if (cudaMemcpy(pl.clouds0.p, ci.data(), (size_t)batch * sizeof(CloudInfo), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(pl.dtile.p, dtile.data(), (size_t)(batch + 1) * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(w.tileoff.p, vtile.data(), (size_t)(batch + 1) * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    return RIPS_ERR_CUDA;
+  }
+  a.clouds = P<CloudInfo>(w.clouds);
+  a.R = P<uint32_t>(w.R);
+  a.nbr_off = P<uint32_t>(w.deg);
+  a.nbr = P<uint32_t>(w.nbr);
+  a.binom = P<uint64_t>(w.binom);
+  a.err = P<uint32_t>(w.err);
+  a.amap_keys = P<uint64_t>(w.amk[0]);
+  a.amap_vals = P<uint64_t>(w.amv[0]);
+  a.amap_mask = pl.acap - 1;
+  pl.blocks = reduction_blocks(a, (uint32_t)E);
+  if (pl.blocks < 1) return RIPS_ERR_CUDA;
+  return RIPS_OK;
+}
+
+// Enqueues the whole forward of a plan on stream s; no host synchronisation,
+// no allocation.
+int plan_run(PlanState& pl, const float* d_points, cudaStream_t s) {
+  Workspace& w = pl.w;
+  const int C = pl.C;
+  const uint64_t E = pl.e_cap, N = pl.N;
+  CloudInfo* dclouds = P<CloudInfo>(w.clouds);
+  unsigned long long* dstats = P<unsigned long long>(w.stats);
+  const float* pts = d_points + (size_t)pl.offsets[0] * pl.k;
+  CK(cudaMemcpyAsync(dclouds, pl.clouds0.p, (size_t)C * sizeof(CloudInfo), cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemsetAsync(w.rowmax.p, 0, N * 4, s));
+  CK(cudaMemsetAsync(w.err.p, 0, 16, s));
+  CK(cudaMemsetAsync(w.ecount.p, 0, 16, s));
+  CK(cudaMemsetAsync(w.ccounts.p, 0, (size_t)(C + 1) * 4, s));
+  CK(cudaMemsetAsync(w.stats.p, 0, (size_t)C * PLAN_SPC * 8, s));
+  CK(cudaMemsetAsync(w.nbars.p, 0, 16, s));
+  CK(launch_distance_matrices(pts, pl.k, dclouds, P<uint32_t>(pl.dtile), C, (uint32_t)pl.drows, P<float>(w.cdist), s));
+  const float* dD = P<float>(w.cdist);
+  // prologue
+  CK(launch_cloud_vertices(dclouds, C, P<uint32_t>(w.vcloud), s));
+  CK(launch_validate_rowmax(dD, dclouds, P<uint32_t>(w.tileoff), C, (uint32_t)pl.vtiles, P<uint32_t>(w.rowmax),
+                            P<uint32_t>(w.err), s));
+  CK(launch_threshold(P<uint32_t>(w.rowmax), dclouds, C, pl.threshold, s));
+  CK(launch_edge_keys(dD, dclouds, P<uint32_t>(w.vcloud), (uint32_t)N, pl.eb, P<uint64_t>(w.ekeys),
+                      P<uint32_t>(w.ecount), P<uint32_t>(w.ccounts), (uint32_t)E, s));
+  CK(launch_cloud_edge_offsets(dclouds, P<uint32_t>(w.ccounts), C, s));
+  CK(launch_pad_past_count(P<uint64_t>(w.ekeys), P<uint32_t>(w.ecount), E, s));
+  bool alt = false;
+  CK(radix_sort_u64(P<uint64_t>(w.ekeys), P<uint64_t>(w.ekeys_alt), nullptr, nullptr, (uint32_t)E,
+                    pl.cb + 32 + pl.eb, w.sorttmp.p, w.sorttmp.cap, &alt, s));
+  const uint64_t* keys = alt ? P<uint64_t>(w.ekeys_alt) : P<uint64_t>(w.ekeys);
+  CK(launch_assign_ranks(keys, (uint32_t)E, pl.eb, P<uint32_t>(w.eflags), (uint32_t*)w.sorttmp.p,
+                         P<uint32_t>(w.erank), P<float>(w.rvalue), &P<uint32_t>(w.ecount)[1], s));
+  CK(cudaMemsetAsync(w.R.p, 0xFF, pl.RR * 4, s));
+  CK(launch_fill_rank_matrix(keys, P<uint32_t>(w.erank), (uint32_t)E, pl.eb, dclouds, P<uint32_t>(w.R), s));
+  CK(cudaMemsetAsync(w.deg.p, 0, (N + 2) * 4, s));
+  CK(launch_neighbor_counts(P<uint32_t>(w.R), dclouds, P<uint32_t>(w.vcloud), (uint32_t)N, P<uint32_t>(w.deg),
+                            &P<uint32_t>(w.ecount)[3], s));
+  CK(launch_exclusive_scan(P<uint32_t>(w.deg), P<uint32_t>(w.deg), (uint32_t)N + 1, w.sorttmp.p,
+                           &P<uint32_t>(w.ecount)[2], s));
+  CK(launch_neighbor_fill(P<uint32_t>(w.R), dclouds, P<uint32_t>(w.vcloud), (uint32_t)N, P<uint32_t>(w.deg),
+                          P<uint32_t>(w.nbr), s));
+  CK(launch_binomial_table(P<uint64_t>(w.binom), pl.n_max, 3, s));
+  // H0, one block per cloud (edges at the cloud table's offsets, set on the device)
+  const uint32_t bar_cap = (uint32_t)(w.bars.cap / sizeof(rips_bar_t));
+  CK(launch_h0_blocks(dclouds, C, pl.n_max, keys, pl.eb, P<uint32_t>(w.eu), P<uint32_t>(w.ev), (uint32_t)E,
+                      P<uint8_t>(w.inforest), P<rips_bar_t>(w.bars), P<uint32_t>(w.nbars), bar_cap, dstats, PLAN_SPC,
+                      P<uint32_t>(w.err), s));
+  // dimension 1 over all E slots (the padding is skipped)
+  const DimArgs& a = pl.a;
+  unsigned long long* st = dstats + 16;
+  CK(launch_edges_to_simplices(keys, P<uint32_t>(w.erank), (uint32_t)E, pl.eb, a.col_bits, P<uint64_t>(w.sidx[0]),
+                               P<uint32_t>(w.srank[0]), s));
+  CK(cudaMemsetAsync(w.ccount.p, 0, 16, s));
+  CK(cudaMemsetAsync(w.amk[0].p, 0xFF, pl.acap * 8, s));
+  CK(launch_test(a, P<uint64_t>(w.sidx[0]), P<uint32_t>(w.srank[0]), (uint32_t)E, P<uint8_t>(w.inforest), nullptr, 0,
+                 P<uint64_t>(w.ckeys), P<uint32_t>(w.ccount), (uint32_t)E + 1, st, PLAN_SPC, s));
+  CK(launch_pad_past_count(P<uint64_t>(w.ckeys), P<uint32_t>(w.ccount), E, s));
+  bool calt = false;
+  CK(radix_sort_u64(P<uint64_t>(w.ckeys), P<uint64_t>(w.ckeys_alt), nullptr, nullptr, (uint32_t)E,
+                    pl.cb + a.rank_bits + a.col_bits, w.sorttmp.p, w.sorttmp.cap, &calt, s));
+  CK(cudaMemsetAsync(w.tkeys[0].p, 0xFF, (size_t)pl.tcap * 8, s));
+  CK(cudaMemsetAsync(w.tvals[0].p, 0xFF, (size_t)pl.tcap * 4, s));
+  CK(cudaMemsetAsync(w.lists.p, 0, 128, s));
+  CK(cudaMemsetAsync(w.r_top.p, 0, 16, s));
+  uint32_t* counts = P<uint32_t>(w.lists);
+  RedState rs;
+  rs.col_keys = calt ? P<uint64_t>(w.ckeys_alt) : P<uint64_t>(w.ckeys);
+  rs.ncols = (uint32_t)E;
+  rs.ncols_dev = P<uint32_t>(w.ccount);
+  rs.piv_key = P<uint64_t>(w.piv_key);
+  rs.piv_coef = P<uint32_t>(w.piv_coef);
+  rs.reduced = P<uint8_t>(w.reduced);
+  rs.r_key = P<uint64_t>(w.r_key);
+  rs.r_coef = P<uint32_t>(w.r_coef);
+  rs.r_off = P<unsigned long long>(w.r_off);
+  rs.r_len = P<uint32_t>(w.r_len);
+  rs.r_top = P<unsigned long long>(w.r_top);
+  rs.r_cap = pl.arena;
+  rs.scr_slice = pl.slice;
+  rs.t_keys = P<uint64_t>(w.tkeys[0]);
+  rs.t_vals = P<uint32_t>(w.tvals[0]);
+  rs.t_mask = pl.tcap - 1;
+  rs.claim_list = P<uint32_t>(w.claim);
+  rs.reduce_list = P<uint32_t>(w.reduce);
+  rs.heavy_list = P<uint32_t>(w.heavy);
+  rs.steps = P<unsigned long long>(w.lists) + 4;
+  rs.compacted = P<unsigned long long>(w.lists) + 5;
+  rs.max_chain = counts + 7;
+  rs.heartbeat = counts + 12;
+  rs.added = P<unsigned long long>(w.lists) + 7;
+  const rips_limits_t lim = current_limits();
+  rs.barrier_ns = lim.barrier_wait_ns ? lim.barrier_wait_ns : 30ull * 1000 * 1000 * 1000;
+  rs.chain_ns = lim.chain_ns ? lim.chain_ns : 600ull * 1000 * 1000 * 1000;
+  rs.err = P<uint32_t>(w.err);
+  CK(launch_reduction(a, rs, pl.blocks, counts, s));
+  CK(launch_readout(a, rs, P<float>(w.rvalue), P<rips_bar_t>(w.bars), P<uint32_t>(w.nbars), bar_cap, st, PLAN_SPC,
+                    s));
+  return RIPS_OK;
+}
+
+// Waits for stream s, then reads the plan's last run back as a result.
+int plan_result(PlanState& pl, cudaStream_t s, rips_result_t** out) {
+  Workspace& w = pl.w;
+  const int C = pl.C;
+  CK(cudaStreamSynchronize(s));
+  uint32_t err = 0, nbars = 0, counts[32] = {};
+  unsigned long long lists[16] = {};
+  std::vector<unsigned long long> hst((size_t)C * PLAN_SPC);
+  std::vector<CloudInfo> ci(C);
+  CK(cudaMemcpy(&err, w.err.p, 4, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&nbars, w.nbars.p, 4, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(counts, w.lists.p, 128, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(lists, w.lists.p, 128, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(hst.data(), w.stats.p, hst.size() * 8, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(ci.data(), w.clouds.p, (size_t)C * sizeof(CloudInfo), cudaMemcpyDeviceToHost));
+  if (err & ERRF_ARENA) return RIPS_ERR_OOM;  // the plan's arena is fixed: make the plan with a larger one
+  if (int e = map_device_error(err)) return e;
+  rips_result* r = new (std::nothrow) rips_result();
+  if (!r) return RIPS_ERR_OOM;
+  r->clouds = C;
+  r->dim_max = 1;
+  r->k = pl.k;
+  r->npoints = pl.ns;
+  r->point_offsets = pl.offsets;
+  r->thresholds.resize(C);
+  r->stats.resize((size_t)C * 2);
+  for (int c = 0; c < C; ++c) {
+    r->thresholds[c] = ci[c].t_eff;
+    const unsigned long long* q0 = hst.data() + (size_t)c * PLAN_SPC;
+    rips_stats_t& s0 = r->stats[(size_t)c * 2];
+    s0.simplices = pl.ns[c];
+    s0.columns = pl.ns[c];
+    s0.pairs = (int64_t)q0[0];
+    s0.zero_pairs = (int64_t)q0[1];
+    s0.essential = (int64_t)q0[2];
+    const unsigned long long* q = q0 + 16;
+    rips_stats_t& sd = r->stats[(size_t)c * 2 + 1];
+    sd.pairs = (int64_t)q[0];
+    sd.zero_pairs = (int64_t)q[1];
+    sd.essential = (int64_t)q[2];
+    sd.emergent = (int64_t)q[3];
+    sd.apparent_cofacet = (int64_t)q[4];
+    sd.apparent_facet = (int64_t)q[5];
+    sd.cleared = (int64_t)q[6];
+    sd.columns = sd.pairs + sd.essential;
+    sd.simplices = sd.apparent_cofacet + sd.apparent_facet + sd.cleared + sd.columns;
+    sd.rounds = counts[6];
+    sd.reduction_steps = (int64_t)lists[4];
+    sd.longest_chain = counts[7];
+    sd.compacted_entries = (int64_t)lists[5];
+    sd.added_entries = (int64_t)lists[7];
+  }
+  const int sbits = std::max(1, bit_width64(host_binom((uint64_t)pl.n_max, 2)));
+  const int rc = finish_bars(w, nbars, sbits, std::max(1, bit_width64((uint64_t)C)), s, r->bars);
+  if (rc != RIPS_OK) {
+    delete r;
+    return rc;
+  }
+  index_result(r);
+  *out = r;
+  return RIPS_OK;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ exported API
@@ -1067,6 +1426,68 @@ RIPS_API int rips_barcodes_backward(const rips_result_t* res, const float* d_poi
   } catch (...) {
     return RIPS_ERR_INTERNAL;
   }
+}
+
+
+struct rips_batch_plan {
+  PlanState st;
+  int device = -1;
+};
+
+RIPS_API int rips_batch_plan_create(const int64_t* offsets, int32_t batch, int32_t k, float threshold, uint32_t p,
+                                    int64_t arena_entries, rips_batch_plan_t** out) {
+  if (!out) return RIPS_ERR_BAD_ARG;
+  *out = nullptr;
+  try {
+    rips_batch_plan* b = new (std::nothrow) rips_batch_plan();
+    if (!b) return RIPS_ERR_OOM;
+    if (cudaGetDevice(&b->device) != cudaSuccess) {
+      cudaGetLastError();
+      delete b;
+      return RIPS_ERR_CUDA;
+    }
+    const int rc = plan_create(b->st, offsets, batch, k, threshold, p, arena_entries);
+    if (rc != RIPS_OK) {
+      release_plan(b->st);
+      delete b;
+      return rc;
+    }
+    *out = b;
+    return RIPS_OK;
+  } catch (...) {
+    return RIPS_ERR_INTERNAL;
+  }
+}
+
+RIPS_API int rips_batch_plan_run(rips_batch_plan_t* plan, const float* d_points, void* cuda_stream) {
+  if (!plan || !d_points) return RIPS_ERR_BAD_ARG;
+  try {
+    std::lock_guard<std::mutex> g(plan->st.w.mu);
+    return plan_run(plan->st, d_points, (cudaStream_t)cuda_stream);
+  } catch (...) {
+    return RIPS_ERR_INTERNAL;
+  }
+}
+
+RIPS_API int rips_batch_plan_result(rips_batch_plan_t* plan, void* cuda_stream, rips_result_t** out) {
+  if (!plan || !out) return RIPS_ERR_BAD_ARG;
+  *out = nullptr;
+  try {
+    std::lock_guard<std::mutex> g(plan->st.w.mu);
+    return plan_result(plan->st, (cudaStream_t)cuda_stream, out);
+  } catch (...) {
+    return RIPS_ERR_INTERNAL;
+  }
+}
+
+RIPS_API void rips_batch_plan_free(rips_batch_plan_t* plan) {
+  if (!plan) return;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) cudaGetLastError();
+  if (plan->device >= 0 && cur != plan->device) cudaSetDevice(plan->device);
+  release_plan(plan->st);
+  if (cur >= 0 && cur != plan->device) cudaSetDevice(cur);
+  delete plan;
 }
 
 }  // extern "C"

@@ -51,6 +51,9 @@
 // end every nonzero column owns its pivot alone, i.e. R is reduced, and by the
 // pivot proposition of Section 3.1 the pairs are exactly those of the
 // sequential algorithm (the pairing of a reduced matrix is unique).
+#include <mutex>
+#include <vector>
+
 #include "rips_internal.cuh"
 
 namespace rips {
@@ -414,6 +417,11 @@ __global__ void edges_to_simplices_kernel(const uint64_t* __restrict__ keys, con
   uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= m) return;
   const uint64_t key = keys[e];
+  if (key == ~0ull) {  // padding past the edge count (batch plans): skipped by the test
+    sidx[e] = ~0ull;
+    srank[e] = 0;
+    return;
+  }
   const uint64_t emask = (1ull << eb) - 1;
   const uint64_t c = key >> (32 + eb);
   sidx[e] = (col_bits >= 64 ? 0ull : (c << col_bits)) | (emask - (key & emask));
@@ -454,6 +462,7 @@ __global__ void __launch_bounds__(256) test_kernel(DimArgs a, const uint64_t* __
   };
   for (uint32_t s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < ns; s += warps) {
     const uint64_t g = sidx[s];
+    if (g == ~0ull) continue;  // padding (batch plans)
     const uint32_t r = srank[s];
     const uint32_t cl = high_part(g, a.col_bits);
     const uint64_t idx = g & low_mask(a.col_bits);
@@ -1952,8 +1961,9 @@ __global__ void __launch_bounds__(256, 2) reduce_persistent_kernel(DimArgs a, Re
   unsigned* light_next = ctl + 18;
   unsigned* heavy_next = ctl + 19;
   uint32_t* heavy[2] = {s.heavy_list, s.heavy_list + (size_t)s.ncols + 1};
+  const uint32_t ncols = s.ncols_dev ? *s.ncols_dev : s.ncols;
 
-  for (uint32_t j = warp_id; j < s.ncols; j += warps)
+  for (uint32_t j = warp_id; j < ncols; j += warps)
     init_column(a, s, B, lane, tile, j, &claim_cnt[0], &heavy_cnt[0], heavy[0]);
   if (!grid_barrier(bar_count, bar_gen, s.heartbeat, s.barrier_ns, a.err)) return;
   uint32_t r = 0;
@@ -2009,7 +2019,8 @@ __global__ void __launch_bounds__(256, 2) reduce_persistent_kernel(DimArgs a, Re
 __global__ void readout_kernel(DimArgs a, RedState s, const float* __restrict__ rank_value,
                                rips_bar_t* __restrict__ bars, uint32_t* __restrict__ nbars, uint32_t bar_cap,
                                unsigned long long* __restrict__ stats, int st_stride) {
-  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < s.ncols; j += gridDim.x * blockDim.x) {
+  const uint32_t ncols = s.ncols_dev ? *s.ncols_dev : s.ncols;
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < ncols; j += gridDim.x * blockDim.x) {
     uint64_t idx;
     uint32_t r, cl;
     column_simplex(a, s, j, &idx, &r, &cl);
@@ -2068,15 +2079,32 @@ static size_t binom_smem(const DimArgs& a) {
 }
 
 // Opt in to more than 48 KB of shared memory when the kernel's static plus
-// dynamic shared memory needs it.
+// dynamic shared memory needs it.  The attributes are queried and set once per
+// kernel, device and size, so launches that are being captured into a CUDA
+// graph make no such calls.
+struct PreparedKernel {
+  const void* fn;
+  int device;
+  size_t smem;
+};
+static std::mutex g_prep_mu;
+static std::vector<PreparedKernel> g_prepared;
+
 template <typename K>
 static cudaError_t prepare(K kernel, size_t smem) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> g(g_prep_mu);
+  for (const PreparedKernel& pk : g_prepared)
+    if (pk.fn == (const void*)kernel && pk.device == dev && pk.smem >= smem) return cudaSuccess;
   cudaFuncAttributes fa;
-  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  e = cudaFuncGetAttributes(&fa, kernel);
   if (e != cudaSuccess) return e;
   if (smem + fa.sharedSizeBytes > 48 * 1024)
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) g_prepared.push_back(PreparedKernel{(const void*)kernel, dev, smem});
+  return e;
 }
 
 cudaError_t launch_enumerate(const DimArgs& a, const uint64_t* pidx, const uint32_t* prank, uint32_t np,

@@ -135,6 +135,8 @@ cudaError_t launch_neighbor_counts(const uint32_t* R, const CloudInfo* clouds, c
 cudaError_t launch_neighbor_fill(const uint32_t* R, const CloudInfo* clouds, const uint32_t* vcloud, uint32_t nverts,
                                  const uint32_t* off, uint32_t* nbr, cudaStream_t s);
 cudaError_t launch_distance_matrix(const float* pts, int n, int k, float* D, cudaStream_t s);
+cudaError_t launch_pad_past_count(uint64_t* keys, const uint32_t* count, uint64_t cap, cudaStream_t s);
+cudaError_t launch_cloud_edge_offsets(CloudInfo* clouds, const uint32_t* ccounts, int nclouds, cudaStream_t s);
 cudaError_t launch_distance_matrices(const float* pts, int k, const CloudInfo* clouds, const uint32_t* tile_off,
                                      int nclouds, uint32_t tiles, float* D, cudaStream_t s);
 
@@ -211,6 +213,7 @@ struct RedState {
   uint32_t* claim_list;
   uint32_t* reduce_list;
   uint32_t* heavy_list;           // two lists of M entries: columns reduced block-wide, by round parity
+  const uint32_t* ncols_dev;      // when set, the column count is read here (ncols is then the capacity)
   unsigned long long* steps;
   unsigned long long* compacted;  // entries read by run compactions (profiling)
   uint32_t* max_chain;            // longest chain of additions (profiling)

@@ -216,6 +216,7 @@ __global__ void fill_rank_matrix_kernel(const uint64_t* __restrict__ keys, const
   uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= m) return;
   const uint64_t key = keys[e];
+  if (key == ~0ull) return;  // padding past the edge count (batch plans)
   const uint64_t emask = (1ull << eb) - 1;
   const uint32_t c = (uint32_t)(key >> (32 + eb));
   const uint64_t idx = emask - (key & emask);
@@ -394,6 +395,44 @@ cudaError_t launch_distance_matrices(const float* pts, int k, const CloudInfo* c
 cudaError_t launch_distance_matrix(const float* pts, int n, int k, float* D, cudaStream_t s) {
   dim3 blk(32, 8), grd((n + 31) / 32, (n + 7) / 8);
   distance_kernel<<<grd, blk, 0, s>>>(pts, n, k, D);
+  note_launch();
+  return cudaGetLastError();
+}
+
+
+// ---------------------------------------------------------------- batch plans (no host reads)
+// Entries [*count, cap) of a key list set to the largest key, so a sort of all
+// cap entries leaves the real ones first.
+__global__ void pad_past_count_kernel(uint64_t* __restrict__ keys, const uint32_t* __restrict__ count, uint64_t cap) {
+  const uint64_t from = *count;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < cap; i += (uint64_t)gridDim.x * blockDim.x)
+    if (i >= from) keys[i] = ~0ull;
+}
+
+// Each cloud's first edge and edge count in the sorted edge list, from the
+// per-cloud counts of the edge-key kernel (one thread: a batch has few clouds).
+__global__ void cloud_edge_offsets_kernel(CloudInfo* __restrict__ clouds, const uint32_t* __restrict__ ccounts,
+                                          int nclouds) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  uint32_t acc = 0;
+  for (int c = 0; c < nclouds; ++c) {
+    clouds[c].eoff = acc;
+    clouds[c].m = ccounts[c];
+    acc += ccounts[c];
+  }
+}
+
+cudaError_t launch_pad_past_count(uint64_t* keys, const uint32_t* count, uint64_t cap, cudaStream_t s) {
+  if (cap == 0) return cudaSuccess;
+  uint64_t blocks = (cap + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  pad_past_count_kernel<<<(unsigned)blocks, 256, 0, s>>>(keys, count, cap);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cloud_edge_offsets(CloudInfo* clouds, const uint32_t* ccounts, int nclouds, cudaStream_t s) {
+  cloud_edge_offsets_kernel<<<1, 32, 0, s>>>(clouds, ccounts, nclouds);
   note_launch();
   return cudaGetLastError();
 }
