@@ -150,6 +150,25 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def measured_traffic(kernel_class: str, workload: str):
+    """DRAM bytes per launch from the committed ncu record (profiles/traffic.json),
+    or None when there is none for this kernel and workload or when the kernel's
+    sources changed since the counters were taken."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f).get(kernel_class)
+        if not rec or rec.get("workload") != workload:
+            return None
+        h = hashlib.sha256()
+        for src in rec["sources"]:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+        return float(rec["bytes_per_launch"]) if h.hexdigest() == rec["source_sha256"] else None
+    except Exception:
+        return None
+
+
 def kernel_roofline(name, km, stats, n, peak, peak_kind):
     """HBM roofline of one kernel class: algorithmic bytes per launch (the
     per-unit figures in the design doc times the units one launch processes) over the
@@ -407,6 +426,8 @@ def main():
     stats = res.stats[0]
     peak, peak_kind = peaks()
     roof = kernel_roofline(dom, km, stats, n, peak, peak_kind)
+    if roof is not None:
+        roof["traffic"] = measured_traffic(dom, w.name)
     streaming = kernel_roofline("apparent", km, stats, n, peak, peak_kind)
     if dom == "reduce":
         # the reduction is bound by its longest chain of dependent additions
