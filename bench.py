@@ -309,6 +309,13 @@ def cpu_baseline(w, budget_s=12.0):
             "sample": f"{runs} full runs of the {w.name} workload (cohomology oracle, {el:.1f} s)"}
 
 
+def workload_config(w, world: int) -> dict:
+    """The config object of both arms' JSON lines (the same workload and conditions)."""
+    return {"workload": w.name, "n": w.n, "dim_max": w.dim_max, "threshold": w.threshold, "p": w.p,
+            "parallelism": f"replicas{world}" if world > 1 else "single",
+            "l2": "flushed between steps (256 MiB write)"}
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -330,8 +337,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": "rips_barcode_simplices_per_s", "value": val, "unit": "simplices/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": {"workload": w.name, "n": w.n, "dim_max": w.dim_max,
-                                             "threshold": w.threshold, "p": w.p, "l2": "n/a (CPU)"},
+            "data": "synthetic", "config": workload_config(w, world),
             "cpu_baseline": {"value": val, "unit": "simplices/s", "cores": 1, "kind": "oracle",
                              "sample": f"the full {w.name} workload per step"},
             "e2e": {"value": val, "unit": "simplices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -462,9 +468,7 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64 integer ranks and indices; f32 values",
                 "data": "synthetic",
-                "config": {"workload": w.name, "n": n, "dim_max": w.dim_max, "threshold": w.threshold, "p": w.p,
-                           "parallelism": f"replicas{world}" if world > 1 else "single",
-                           "l2": "flushed between steps (256 MiB write)"},
+                "config": workload_config(w, world),
                 "per_dim": per_dim, "barcode_ms": ms_per_step, "bars": nbars,
                 "kernel_ms": {k: v[0] for k, v in km.items()},
                 "roofline": roof, "roofline_streaming": streaming, "cpu_baseline": cpu, "e2e": e2e,
