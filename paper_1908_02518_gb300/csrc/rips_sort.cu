@@ -235,10 +235,57 @@ size_t sort_temp_bytes(uint32_t n) {
   return (tiles * RADIX + RADIX) * sizeof(uint32_t);
 }
 
+// Up to SMALL_SORT keys without values: one block sorts them in shared memory
+// with a bitonic network, in one launch instead of three per radix digit.
+// Without values the order of equal keys does not show, so the result is the
+// radix sort's.
+constexpr uint32_t SMALL_SORT = 8192;
+
+__global__ void __launch_bounds__(1024) sort_small_kernel(uint64_t* __restrict__ keys, uint32_t n, uint32_t n2) {
+  extern __shared__ uint64_t k[];
+  for (uint32_t i = threadIdx.x; i < n2; i += blockDim.x) k[i] = i < n ? keys[i] : ~0ull;
+  __syncthreads();
+  for (uint32_t size = 2; size <= n2; size <<= 1) {
+    for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+      for (uint32_t i = threadIdx.x; i < n2; i += blockDim.x) {
+        const uint32_t l = i ^ stride;
+        if (l > i) {
+          const uint64_t a = k[i], b = k[l];
+          if ((a > b) == ((i & size) == 0)) {
+            k[i] = b;
+            k[l] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) keys[i] = k[i];
+}
+
 cudaError_t radix_sort_u64(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t* vals_alt, uint32_t n,
                            int key_bits, void* tmp, size_t tmp_bytes, bool* result_in_alt, cudaStream_t s) {
   *result_in_alt = false;
   if (n <= 1 || key_bits <= 0) return cudaSuccess;
+  if (!vals && n <= SMALL_SORT) {
+    uint32_t n2 = 2;
+    while (n2 < n) n2 <<= 1;
+    const size_t smem = (size_t)n2 * 8;
+    if (smem > 48 * 1024) {
+      static bool opted[64] = {};  // once per device
+      int dev = 0;
+      cudaError_t e = cudaGetDevice(&dev);
+      if (e != cudaSuccess) return e;
+      if (dev < 0 || dev >= 64 || !opted[dev]) {
+        e = cudaFuncSetAttribute(sort_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SMALL_SORT * 8));
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) opted[dev] = true;
+      }
+    }
+    sort_small_kernel<<<1, 1024, smem, s>>>(keys, n, n2);
+    note_launch();
+    return cudaGetLastError();
+  }
   uint32_t tiles = (uint32_t)(((size_t)n + RS_TILE - 1) / RS_TILE);
   if (tmp_bytes < sort_temp_bytes(n)) return cudaErrorInvalidValue;
   uint32_t* hist = (uint32_t*)tmp;
