@@ -731,46 +731,104 @@ __device__ void warp_sort_pairs(uint64_t* key, uint32_t* coef, uint32_t n, int l
 // warp reductions, and the heads at a key whose coefficients cancel move on:
 // the paper's lazily evaluated working coboundary (Section 4, "Pivot
 // extraction"), with sorted runs in place of its heap.  Runs are merged size-
-// tiered: when four runs fall in the same size class (sizes within a factor of
-// four), they become one, so an entry is merged a logarithmic number of times
-// however long the chain; at the end of a chain the column is merged into one
-// run, which later columns add.
+// tiered: when four runs (eight short ones) fall in the same size class
+// (sizes within a factor of four), they become one, so an entry is merged a
+// logarithmic number of times however long the chain; at the end of a chain
+// the column is merged into one run, which later columns add.
+//
+// Each run keeps the RUN_AHEAD entries after its head (key and stored
+// coefficient) in registers, loaded that many steps before they are needed.
+constexpr int RUN_AHEAD = 1;
+
 struct Run {
   const uint64_t* key;
   const uint32_t* coef;
   uint32_t len, cur, scale;
-  uint64_t hk;  // head key, ~0 once the run is used up
-  uint32_t hc;  // head coefficient times scale, mod p (1 over Z/2)
-  uint64_t nk;  // the key after the head, loaded ahead of time
+  uint64_t hk;             // head key, ~0 once the run is used up
+  uint32_t hc;             // head coefficient times scale, mod p (1 over Z/2)
+  uint64_t nk[RUN_AHEAD];  // the keys after the head (~0 past the end)
+  uint32_t nc[RUN_AHEAD];  // and their stored coefficients (not loaded over Z/2)
 };
 
-// head coefficient (over Z/2 every stored coefficient is 1)
-__device__ __forceinline__ uint32_t run_coef(const Run& r, uint32_t p) {
-  return p == 2 ? 1u : (uint32_t)(((uint64_t)r.coef[r.cur] * r.scale) % p);
+__device__ __forceinline__ uint32_t scaled(uint32_t c, uint32_t scale, uint32_t p) {
+  return p == 2 ? 1u : (uint32_t)(((uint64_t)c * scale) % p);
 }
 
+// head and look-ahead from the cursor on
 __device__ __forceinline__ void run_head(Run& r, uint32_t p) {
   r.hk = r.cur < r.len ? r.key[r.cur] : ~0ull;
-  r.hc = r.cur < r.len ? run_coef(r, p) : 0u;
-  r.nk = r.cur + 1 < r.len ? r.key[r.cur + 1] : ~0ull;
+  r.hc = r.cur < r.len ? scaled(p == 2 ? 1u : r.coef[r.cur], r.scale, p) : 0u;
+#pragma unroll
+  for (int i = 0; i < RUN_AHEAD; ++i) {
+    const bool in = r.cur + 1 + i < r.len;
+    r.nk[i] = in ? r.key[r.cur + 1 + i] : ~0ull;
+    r.nc[i] = in && p != 2 ? r.coef[r.cur + 1 + i] : 1u;
+  }
 }
 
-// move to the next entry; its key was loaded ahead, the one after is requested now
+// move to the next entry, loaded ahead; the entry RUN_AHEAD past it is requested now
 __device__ __forceinline__ void run_next(Run& r, uint32_t p) {
   ++r.cur;
-  r.hk = r.nk;
-  r.hc = r.cur < r.len ? run_coef(r, p) : 0u;
-  r.nk = r.cur + 1 < r.len ? r.key[r.cur + 1] : ~0ull;
+  r.hk = r.nk[0];
+  r.hc = r.cur < r.len ? scaled(r.nc[0], r.scale, p) : 0u;
+#pragma unroll
+  for (int i = 0; i + 1 < RUN_AHEAD; ++i) {
+    r.nk[i] = r.nk[i + 1];
+    r.nc[i] = r.nc[i + 1];
+  }
+  const bool in = r.cur + RUN_AHEAD < r.len;
+  r.nk[RUN_AHEAD - 1] = in ? r.key[r.cur + RUN_AHEAD] : ~0ull;
+  r.nc[RUN_AHEAD - 1] = in && p != 2 ? r.coef[r.cur + RUN_AHEAD] : 1u;
 }
 
-__device__ __forceinline__ Run make_run(const uint64_t* k, const uint32_t* c, uint32_t n, uint32_t scale,
-                                        uint32_t p) {
-  Run r{k, c, n, 0, scale, ~0ull, 0, ~0ull};
-  run_head(r, p);
+__device__ __forceinline__ Run empty_run() {
+  Run r;
+  r.key = nullptr;
+  r.coef = nullptr;
+  r.len = r.cur = 0;
+  r.scale = 1;
+  r.hk = ~0ull;
+  r.hc = 0;
+#pragma unroll
+  for (int i = 0; i < RUN_AHEAD; ++i) {
+    r.nk[i] = ~0ull;
+    r.nc[i] = 1u;
+  }
   return r;
 }
 
-__device__ __forceinline__ Run empty_run() { return Run{nullptr, nullptr, 0, 0, 1, ~0ull, 0, ~0ull}; }
+// A run over n arena entries.  When the block has the first entries in shared
+// memory (sk, sc: the same keys and coefficients), the head and look-ahead are
+// taken from there instead of waiting for the arena.
+__device__ __forceinline__ Run make_run(const uint64_t* k, const uint32_t* c, uint32_t n, uint32_t scale,
+                                        uint32_t p, const uint64_t* sk = nullptr, const uint32_t* sc = nullptr) {
+  Run r = empty_run();
+  r.key = k;
+  r.coef = c;
+  r.len = n;
+  r.scale = scale;
+  if (sk) {
+    r.hk = n ? sk[0] : ~0ull;
+    r.hc = n ? scaled(sc[0], scale, p) : 0u;
+#pragma unroll
+    for (int i = 0; i < RUN_AHEAD; ++i) {
+      const bool in = 1u + i < n;
+      r.nk[i] = in ? sk[1 + i] : ~0ull;
+      r.nc[i] = in ? sc[1 + i] : 1u;
+    }
+  } else {
+    run_head(r, p);
+  }
+  return r;
+}
+
+// run_next on the lanes where `at` holds, without a divergent branch: every
+// lane computes its next state (its loads stay inside its run) and keeps it or not
+__device__ __forceinline__ void advance_if(Run& r, bool at, uint32_t p) {
+  Run t = r;
+  run_next(t, p);
+  if (at) r = t;
+}
 
 // combined coefficient of the lanes at the current minimum (`at`)
 __device__ __forceinline__ uint32_t warp_coef_sum(bool at, uint32_t hc, uint32_t p) {
@@ -855,7 +913,7 @@ __device__ uint64_t runs_pivot(Run& r, uint32_t p, uint32_t* coef_out) {
       *coef_out = c;
       return m;
     }
-    if (at) run_next(r, p);
+    advance_if(r, at, p);
   }
 }
 
@@ -872,19 +930,34 @@ __device__ void runs_pack(Run& r, int lane, int* nr) {
   t.scale = __shfl_sync(0xffffffffu, r.scale, src);
   t.hk = __shfl_sync(0xffffffffu, r.hk, src);
   t.hc = __shfl_sync(0xffffffffu, r.hc, src);
-  t.nk = __shfl_sync(0xffffffffu, r.nk, src);
+#pragma unroll
+  for (int i = 0; i < RUN_AHEAD; ++i) {
+    t.nk[i] = __shfl_sync(0xffffffffu, r.nk[i], src);
+    t.nc[i] = __shfl_sync(0xffffffffu, r.nc[i], src);
+  }
   r = lane < cnt ? t : empty_run();
   *nr = cnt;
 }
 
-// Runs to merge now: a size class holding four runs, or every run when all 32
-// lanes are taken; 0 when none.
+// Runs to merge now: a size class holding MERGE_GROUP runs (MERGE_GROUP_SHORT
+// for the classes of runs shorter than 4^(SHORT_TIERS), where a merge costs
+// more than the entries it saves), or, when all 32 lanes are taken, the size
+// class holding the most runs (the shortest of those); 0 when none.
+constexpr int MERGE_GROUP = 4;
+constexpr int MERGE_GROUP_SHORT = 8;
+constexpr int SHORT_TIERS = 4;  // runs of fewer than 256 entries
+
 __device__ unsigned runs_merge_mask(const Run& r, int lane, int nr) {
   const int t = lane < nr ? run_tier(r) : -1;
   const unsigned grp = __match_any_sync(0xffffffffu, t >= 0 ? t : -2 - lane);
-  const unsigned elig = __ballot_sync(0xffffffffu, t >= 0 && __popc(grp) >= 4);
+  const unsigned elig =
+      __ballot_sync(0xffffffffu, t >= 0 && __popc(grp) >= (t < SHORT_TIERS ? MERGE_GROUP_SHORT : MERGE_GROUP));
   if (elig) return __shfl_sync(0xffffffffu, grp, __ffs(elig) - 1);
-  if (nr == 32) return __ballot_sync(0xffffffffu, t >= 0);
+  if (nr == 32) {
+    const unsigned score = t >= 0 ? ((unsigned)__popc(grp) << 8) | (255u - (unsigned)t) : 0u;
+    const unsigned best = __reduce_max_sync(0xffffffffu, score);
+    return __shfl_sync(0xffffffffu, grp, __ffs(__ballot_sync(0xffffffffu, score == best)) - 1);
+  }
   return 0;
 }
 
@@ -905,7 +978,7 @@ __device__ bool runs_merge_warp(const RedState& s, Run& r, int lane, uint32_t p,
     if (m == ~0ull) break;
     const bool at = h == m;
     const uint32_t c = warp_coef_sum(at, r.hc, p);
-    if (at) run_next(r, p);
+    advance_if(r, at, p);
     if (c) {
       if (lane == 0) {
         ok[out] = m;
@@ -947,9 +1020,10 @@ struct ChainReq {
 // R_j <- R_j - lambda C, lambda = pivot coefficient ratio (Algorithm 1): the run
 // of C joins the set, then the new pivot is found
 __device__ __forceinline__ void chain_add(const DimArgs& a, const RedState& s, Chain& ch, int lane,
-                                          const uint64_t* wk, const uint32_t* wc, uint32_t wn, uint32_t wcoef) {
+                                          const uint64_t* wk, const uint32_t* wc, uint32_t wn, uint32_t wcoef,
+                                          const uint64_t* sk = nullptr, const uint32_t* sc = nullptr) {
   const uint32_t lam = (uint32_t)(((uint64_t)ch.coef * mod_inv(wcoef, a.p)) % a.p);
-  if (lane == ch.nr) ch.r = make_run(wk, wc, wn, (a.p - lam) % a.p, a.p);
+  if (lane == ch.nr) ch.r = make_run(wk, wc, wn, (a.p - lam) % a.p, a.p, sk, sc);
   ++ch.nr;
   ++ch.step;
   if (lane == 0) {
@@ -1320,10 +1394,12 @@ __device__ void block_bitonic(uint64_t* key, uint32_t* coef, uint32_t n2) {
 // blockDim.x cofacets are then placed by rank (each thread counts the smaller
 // keys; the keys are distinct) straight into their arena slots, reserved at
 // the start; more are sorted by a bitonic network (in an arena buffer past
-// GEN_SMEM_CAP) and copied.  *out gets the run (scale 1).  Called by the whole
-// block; false (in every thread) when the arena is full.
+// GEN_SMEM_CAP) and copied.  *out gets the run (scale 1) and *sk, *sc a
+// sorted copy in shared memory (null when the sort ran in the arena).  Called by
+// the whole block; false (in every thread) when the arena is full.
 __device__ bool block_gen_sorted(const DimArgs& a, const RedState& s, const CV& cv, const Binom& B,
-                                 unsigned char* raw, MergeReq& q, uint64_t idx, uint32_t rank, RunDesc* out) {
+                                 unsigned char* raw, MergeReq& q, uint64_t idx, uint32_t rank, RunDesc* out,
+                                 const uint64_t** sk, const uint32_t** sc) {
   const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int d = a.d;
   int v[MAX_DIM + 2];
@@ -1375,15 +1451,22 @@ __device__ bool block_gen_sorted(const DimArgs& a, const RedState& s, const CV& 
   const unsigned long long off = q.off;
   if (off + want > s.r_cap) return false;
   if (!in_arena && cnt <= blockDim.x) {
-    if (tid < cnt) {  // rank placement
+    static_assert(GEN_SMEM_CAP >= 512, "the sorted copy follows the unsorted entries");
+    if (tid < cnt) {  // rank placement, into the arena and into a copy past the first blockDim.x entries
       const uint64_t k = bk[tid];
+      const uint32_t cf = bc[tid];
       uint32_t rk = 0;
+#pragma unroll 8
       for (uint32_t u = 0; u < cnt; ++u) rk += bk[u] < k;
       s.r_key[off + rk] = k;
-      s.r_coef[off + rk] = bc[tid];
+      s.r_coef[off + rk] = cf;
+      bk[blockDim.x + rk] = k;
+      bc[blockDim.x + rk] = cf;
     }
     __syncthreads();
     *out = RunDesc{s.r_key + off, s.r_coef + off, cnt, 1};
+    *sk = bk + blockDim.x;
+    *sc = bc + blockDim.x;
     return true;
   }
   uint32_t n2 = 1;
@@ -1396,8 +1479,12 @@ __device__ bool block_gen_sorted(const DimArgs& a, const RedState& s, const CV& 
   block_bitonic(bk, bc, n2);
   if (in_arena) {
     *out = RunDesc{bk, bc, cnt, 1};
+    *sk = nullptr;
+    *sc = nullptr;
     return true;
   }
+  *sk = bk;
+  *sc = bc;
   for (uint32_t i = tid; i < cnt; i += blockDim.x) {
     s.r_key[off + i] = bk[i];
     s.r_coef[off + i] = bc[i];
@@ -1859,17 +1946,19 @@ __device__ void reduce_one_block(const DimArgs& a, const RedState& s, const Bino
       }
     } else if (state == CH_GEN || state == CH_GEN_SELF) {
       RunDesc g;
-      if (!block_gen_sorted(a, s, cv, B, raw, q, q.gidx, q.grank, &g)) {
+      const uint64_t* gk;
+      const uint32_t* gc;
+      if (!block_gen_sorted(a, s, cv, B, raw, q, q.gidx, q.grank, &g, &gk, &gc)) {
         state = CH_ARENA;
         break;
       }
       if (tid < 32) {
         if (state == CH_GEN_SELF) {
-          if (lane == 0) ch.r = make_run(g.key, g.coef, g.len, 1, a.p);
+          if (lane == 0) ch.r = make_run(g.key, g.coef, g.len, 1, a.p, gk, gc);
           ch.nr = 1;
           ch.started = true;
         } else {
-          chain_add(a, s, ch, lane, g.key, g.coef, g.len, ch.pcoef);
+          chain_add(a, s, ch, lane, g.key, g.coef, g.len, ch.pcoef, gk, gc);
         }
       }
     } else {
