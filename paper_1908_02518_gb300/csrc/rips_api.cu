@@ -96,7 +96,7 @@ struct Workspace {
   Buf piv_key, piv_coef, r_off, r_len, reduced, claim, reduce, heavy, lists;
   Buf r_key, r_coef, r_top;
   Buf tkeys[2], tvals[2];
-  Buf amk[2], amv[2];  // apparent-pair maps of dimensions d and d - 1
+  Buf amk[2];  // apparent-pair maps of dimensions d and d - 1 ((key, value) pairs)
   Buf bars, bars_alt, bk0, bk1, bp0, bp1, bartmp, nbars;
   Buf stats, bwd_bars, bwd_off, cdist, clouds, tileoff, vcloud, ccounts;
   size_t r_cap = 0;
@@ -479,10 +479,9 @@ int run_batch(Workspace& w, const float* dD, const std::vector<int64_t>& ns, int
     a.rank_bits = rank_bits;
     a.rank_max = num_ranks ? num_ranks - 1 : 0;
     a.err = P<uint32_t>(w.err);
-    a.amap_keys = nullptr;
-    a.amap_vals = nullptr;
+    a.amap = nullptr;
     a.amap_mask = 0;
-    a.pmap_keys = prev_amap;
+    a.pmap = prev_amap;
     a.pmap_mask = prev_amask;
     {
       const rips_tuning_t tu = tuning_for(d, n_max);
@@ -538,11 +537,9 @@ int run_batch(Workspace& w, const float* dD, const std::vector<int64_t>& ns, int
     uint64_t acap = 16;
     while (acap < 2ull * nsd + 16) acap <<= 1;
     if (a.col_bits <= 60 && acap * 16 <= (16ull << 30)) {  // else the test and reduction scan instead
-      CR(ensure(w.amk[cur], (size_t)acap * 8));
-      CR(ensure(w.amv[cur], (size_t)acap * 8));
-      CK(cudaMemsetAsync(w.amk[cur].p, 0xFF, (size_t)acap * 8, s));
-      a.amap_keys = P<uint64_t>(w.amk[cur]);
-      a.amap_vals = P<uint64_t>(w.amv[cur]);
+      CR(ensure(w.amk[cur], (size_t)acap * 16));
+      CK(cudaMemsetAsync(w.amk[cur].p, 0xFF, (size_t)acap * 16, s));
+      a.amap = P<uint64_t>(w.amk[cur]);
       a.amap_mask = acap - 1;
     }
     {
@@ -663,7 +660,7 @@ int run_batch(Workspace& w, const float* dD, const std::vector<int64_t>& ns, int
     }
     if (!done) return RIPS_ERR_OOM;
     prev_tkeys = P<uint64_t>(w.tkeys[tb]);
-    prev_amap = a.amap_keys;
+    prev_amap = a.amap;
     prev_amask = a.amap_mask;
     prev_tmask = tcap - 1;
     ns_prev = nsd;
@@ -915,7 +912,7 @@ void release_plan(PlanState& pl) {
                 &w.gtop, &w.inforest, &w.fpos, &w.nf, &w.sidx[0], &w.sidx[1], &w.srank[0], &w.srank[1],
                 &w.scount, &w.ckeys, &w.ckeys_alt, &w.ccount, &w.sorttmp, &w.piv_key, &w.piv_coef, &w.r_off,
                 &w.r_len, &w.reduced, &w.claim, &w.reduce, &w.heavy, &w.lists, &w.r_key, &w.r_coef, &w.r_top,
-                &w.tkeys[0], &w.tkeys[1], &w.tvals[0], &w.tvals[1], &w.amk[0], &w.amk[1], &w.amv[0], &w.amv[1],
+                &w.tkeys[0], &w.tkeys[1], &w.tvals[0], &w.tvals[1], &w.amk[0], &w.amk[1],
                 &w.bars, &w.bars_alt, &w.bk0, &w.bk1, &w.bp0, &w.bp1, &w.bartmp, &w.nbars, &w.stats,
                 &w.bwd_bars, &w.bwd_off, &w.cdist, &w.clouds, &w.tileoff, &w.vcloud, &w.ccounts, &pl.clouds0,
                 &pl.dtile};
@@ -979,7 +976,7 @@ int plan_create(PlanState& pl, const int64_t* offsets, int32_t batch, int32_t k,
     a.reduce_blocks_per_sm = tu.reduce_blocks_per_sm;
     a.scan_blocks_per_sm = tu.scan_blocks_per_sm;
   }
-  a.pmap_keys = nullptr;
+  a.pmap = nullptr;
   a.pmap_mask = 0;
   pl.tcap = pow2_at_least(2ull * pl.e_cap + 16);
   pl.acap = pow2_at_least(2ull * pl.e_cap + 16);
@@ -1029,8 +1026,7 @@ int plan_create(PlanState& pl, const int64_t* offsets, int32_t batch, int32_t k,
   CR(ensure(w.ckeys, (E + 1) * 8));
   CR(ensure(w.ckeys_alt, (E + 1) * 8));
   CR(ensure(w.ccount, 16));
-  CR(ensure(w.amk[0], pl.acap * 8));
-  CR(ensure(w.amv[0], pl.acap * 8));
+  CR(ensure(w.amk[0], pl.acap * 16));
   CR(ensure(w.tkeys[0], (size_t)pl.tcap * 8));
   CR(ensure(w.tvals[0], (size_t)pl.tcap * 4));
   CR(ensure(w.piv_key, (E + 1) * 8));
@@ -1058,8 +1054,7 @@ int plan_create(PlanState& pl, const int64_t* offsets, int32_t batch, int32_t k,
   a.nbr = P<uint32_t>(w.nbr);
   a.binom = P<uint64_t>(w.binom);
   a.err = P<uint32_t>(w.err);
-  a.amap_keys = P<uint64_t>(w.amk[0]);
-  a.amap_vals = P<uint64_t>(w.amv[0]);
+  a.amap = P<uint64_t>(w.amk[0]);
   a.amap_mask = pl.acap - 1;
   pl.blocks = reduction_blocks(a, (uint32_t)E);
   if (pl.blocks < 1) return RIPS_ERR_CUDA;
@@ -1120,7 +1115,7 @@ int plan_run(PlanState& pl, const float* d_points, cudaStream_t s) {
   CK(launch_edges_to_simplices(keys, P<uint32_t>(w.erank), (uint32_t)E, pl.eb, a.col_bits, P<uint64_t>(w.sidx[0]),
                                P<uint32_t>(w.srank[0]), s));
   CK(cudaMemsetAsync(w.ccount.p, 0, 16, s));
-  CK(cudaMemsetAsync(w.amk[0].p, 0xFF, pl.acap * 8, s));
+  CK(cudaMemsetAsync(w.amk[0].p, 0xFF, pl.acap * 16, s));
   CK(launch_test(a, P<uint64_t>(w.sidx[0]), P<uint32_t>(w.srank[0]), (uint32_t)E, P<uint8_t>(w.inforest), nullptr, 0,
                  P<uint64_t>(w.ckeys), P<uint32_t>(w.ccount), (uint32_t)E + 1, st, PLAN_SPC, s));
   CK(launch_pad_past_count(P<uint64_t>(w.ckeys), P<uint32_t>(w.ccount), E, s));

@@ -339,6 +339,37 @@ __device__ __forceinline__ int64_t table_insert(uint64_t* keys, uint64_t cap_mas
   return -1;
 }
 
+// (key, value) pair tables: slot h is kv[2h] (key, IDX_NONE when empty) and
+// kv[2h + 1] (value), so a probe reads both in one 16-byte load
+__device__ __forceinline__ int64_t pair_insert(uint64_t* kv, uint64_t cap_mask, uint64_t key) {
+  uint64_t h = mix(key) & cap_mask;
+  for (uint64_t probe = 0; probe <= cap_mask; ++probe) {
+    const uint64_t cur = kv[2 * h];
+    if (cur == key) return (int64_t)h;
+    if (cur == IDX_NONE) {
+      const uint64_t old =
+          atomicCAS((unsigned long long*)&kv[2 * h], (unsigned long long)IDX_NONE, (unsigned long long)key);
+      if (old == IDX_NONE || old == key) return (int64_t)h;
+    }
+    h = (h + 1) & cap_mask;
+  }
+  return -1;
+}
+
+__device__ __forceinline__ bool pair_find(const uint64_t* kv, uint64_t cap_mask, uint64_t key, uint64_t* val) {
+  uint64_t h = mix(key) & cap_mask;
+  for (uint64_t probe = 0; probe <= cap_mask; ++probe) {
+    const ulonglong2 e = *reinterpret_cast<const ulonglong2*>(kv + 2 * h);
+    if (e.x == key) {
+      *val = e.y;
+      return true;
+    }
+    if (e.x == IDX_NONE) return false;
+    h = (h + 1) & cap_mask;
+  }
+  return false;
+}
+
 __device__ __forceinline__ int64_t table_find(const uint64_t* keys, uint64_t cap_mask, uint64_t key) {
   if (cap_mask == 0 && keys == nullptr) return -1;
   uint64_t h = mix(key) & cap_mask;
@@ -502,15 +533,15 @@ __global__ void __launch_bounds__(256) test_kernel(DimArgs a, const uint64_t* __
       app = __shfl_sync(0xffffffffu, app, hl);
       if (app) {
         ++n_cof;
-        if (lane == 0 && a.amap_keys) {  // tau -> sigma, for the reduction and the next dimension
+        if (lane == 0 && a.amap) {  // tau -> sigma, for the reduction and the next dimension
           CofacetSums cs;
           cofacet_sums(B, v, d, cs);
           int c = 0;
           for (int l = 0; l <= d; ++l) c += v[l] > j;
           const uint64_t tidx = cs.above[c] + B(j, d + 2 - c) + cs.below[c];
-          const int64_t slot = table_insert(a.amap_keys, a.amap_mask, table_key(a, cl, tidx));
+          const int64_t slot = pair_insert(a.amap, a.amap_mask, table_key(a, cl, tidx));
           if (slot < 0) set_error(a.err, ERRF_TABLE_FULL);
-          else a.amap_vals[slot] = (idx << 4) | (uint64_t)c;
+          else a.amap[2 * slot + 1] = (idx << 4) | (uint64_t)c;
         }
         continue;
       }
@@ -519,8 +550,9 @@ __global__ void __launch_bounds__(256) test_kernel(DimArgs a, const uint64_t* __
     // the previous dimension's test recorded every zero apparent pair
     if (d >= 2) {
       bool fac;
-      if (a.pmap_keys) {
-        fac = table_find(a.pmap_keys, a.pmap_mask, g) >= 0;
+      if (a.pmap) {
+        uint64_t unused;
+        fac = pair_find(a.pmap, a.pmap_mask, g, &unused);
       } else {
         uint32_t minus[MAX_DIM + 2];
         ranks_minus_one(cv.R, cv.n, v, d, minus);
@@ -619,10 +651,9 @@ __device__ void min_entry(const DimArgs& a, const CV& cv, const Binom& B, int la
 __device__ uint64_t pivot_apparent_facet(const DimArgs& a, const CV& cv, const Binom& B, int lane, uint32_t cl,
                                          uint64_t key, uint32_t* frank, uint32_t* tcoef) {
   const int k = a.d + 1;
-  if (a.amap_keys) {  // recorded by this dimension's test kernel
-    const int64_t slot = table_find(a.amap_keys, a.amap_mask, table_key(a, cl, row_key_idx(a, key)));
-    if (slot < 0) return IDX_NONE;
-    const uint64_t v = a.amap_vals[slot];
+  if (a.amap) {  // recorded by this dimension's test kernel
+    uint64_t v;
+    if (!pair_find(a.amap, a.amap_mask, table_key(a, cl, row_key_idx(a, key)), &v)) return IDX_NONE;
     *frank = row_key_rank(a, key);
     *tcoef = ((a.d - (int)(v & 15)) & 1) ? a.p - 1 : 1u;
     return v >> 4;
@@ -1362,7 +1393,26 @@ struct MergeReq {
   uint32_t roff[33];  // run offsets of a merge staged in shared memory
   unsigned long long off;
   uint32_t take;  // the heavy column this block takes next
+  // arena slots reserved by this block for generated coboundaries and not yet used
+  unsigned long long chunk_off, chunk_left;
 };
+
+// Block mode takes arena slots (for generated coboundaries and merges) from a
+// block-local chunk of at least GEN_CHUNK entries, so most requests make no
+// global atomic.  Called by one thread; the slots start at q.off.  Whether they
+// lie inside the arena is checked by the caller (q.off + want <= r_cap).
+constexpr unsigned long long GEN_CHUNK = 4096;
+
+__device__ __forceinline__ void block_reserve(const RedState& s, MergeReq& q, unsigned long long want) {
+  if (want > q.chunk_left) {
+    const unsigned long long grab = want > GEN_CHUNK ? want : GEN_CHUNK;
+    q.chunk_off = atomicAdd(s.r_top, grab);
+    q.chunk_left = grab;
+  }
+  q.off = q.chunk_off;
+  q.chunk_off += want;
+  q.chunk_left -= want;
+}
 
 constexpr uint32_t GEN_SMEM_CAP = (uint32_t)(RED_SMEM_BYTES / 12);  // generated entries sorted in shared memory
 
@@ -1414,7 +1464,7 @@ __device__ bool block_gen_sorted(const DimArgs& a, const RedState& s, const CV& 
   const bool in_arena = p2 > GEN_SMEM_CAP;
   // the output slots (and the sort buffer when it does not fit in shared memory)
   const unsigned long long want = in_arena ? p2 : (deg ? deg : 1);
-  if (tid == 0) q.off = atomicAdd(s.r_top, want);
+  if (tid == 0) block_reserve(s, q, want);
   uint64_t* bk = (uint64_t*)raw;
   uint32_t* bc = (uint32_t*)(raw + (size_t)GEN_SMEM_CAP * 8);
   if (in_arena) {
@@ -1616,7 +1666,7 @@ __device__ bool block_merge_small(const RedState& s, unsigned char* raw, MergeRe
   uint64_t* ok = (uint64_t*)(raw + SMALL_MERGE * 8);                   // sorted keys
   uint32_t* sc = (uint32_t*)(raw + SMALL_MERGE * 16);                  // loaded coefficients (scaled)
   uint32_t* oc = (uint32_t*)(raw + SMALL_MERGE * 16 + SMALL_MERGE * 4);  // sorted coefficients
-  if (tid == 0) q.off = atomicAdd(s.r_top, (unsigned long long)(total ? total : 1));
+  if (tid == 0) block_reserve(s, q, total ? total : 1);
   for (uint32_t e = tid; e < total; e += blockDim.x) {
     uint32_t r = 0, pre = 0;
     while (e >= pre + q.d[r].len) pre += q.d[r++].len;
@@ -1801,7 +1851,7 @@ __device__ int block_merge_chunked(const RedState& s, unsigned char* raw, MergeR
   if (K > MERGE_CHUNKS) return -1;
   // arena: scratch for one chunk, the output, and the chunk boundaries
   const unsigned long long want = (unsigned long long)MID_MERGE + total + (unsigned long long)K * n;
-  if (tid == 0) q.off = atomicAdd(s.r_top, want);
+  if (tid == 0) block_reserve(s, q, want);
   __syncthreads();
   const unsigned long long off = q.off;
   if (off + want > s.r_cap) return 0;
@@ -1863,7 +1913,7 @@ __device__ bool block_merge_runs(const RedState& s, MergeSmem& ms, MergeReq& q, 
       const RunDesc A = q.d[2 * i];
       const RunDesc Bd = n > 1 ? q.d[2 * i + 1] : none;
       const unsigned long long want = (unsigned long long)A.len + Bd.len;
-      if (threadIdx.x == 0) q.off = atomicAdd(s.r_top, want ? want : 1ull);
+      if (threadIdx.x == 0) block_reserve(s, q, want ? want : 1ull);
       __syncthreads();
       const unsigned long long off = q.off;
       if (off + want > s.r_cap) return false;
@@ -2039,6 +2089,7 @@ __global__ void __launch_bounds__(256, 2) reduce_persistent_kernel(DimArgs a, Re
   // the warps' sort tiles, or one merge tile for the whole block in block mode
   __shared__ __align__(16) unsigned char red_smem[RED_SMEM_BYTES];
   __shared__ MergeReq req;
+  if (threadIdx.x == 0) req.chunk_left = 0;  // visible to the block after the first grid barrier
   const uint32_t w = threadIdx.x >> 5;
   const SortTile tile{(uint64_t*)red_smem + w * SORT_TILE,
                       (uint32_t*)(red_smem + (size_t)WARPS_PER_BLOCK * SORT_TILE * 8) + w * SORT_TILE};

@@ -171,14 +171,15 @@ struct DimArgs {
   uint32_t rank_max;               // largest diameter rank
   uint32_t* err;
   // zero-persistence apparent pairs (sigma, tau) with sigma a d-simplex, written
-  // by the test kernel: key (cloud << row_bits) | idx(tau), value
-  // (idx(sigma) << 4) | position of the vertex tau has beyond sigma; null when
-  // col_bits > 60 (the index does not fit beside the position)
-  uint64_t* amap_keys;
-  uint64_t* amap_vals;
+  // by the test kernel: a hash table of (key, value) pairs, slot h at amap[2h]
+  // and amap[2h + 1] (one 16-byte load reads both), amap_mask + 1 slots; key
+  // (cloud << row_bits) | idx(tau), value (idx(sigma) << 4) | position of the
+  // vertex tau has beyond sigma; null when col_bits > 60 (the index does not
+  // fit beside the position)
+  uint64_t* amap;
   uint64_t amap_mask;
   // the same map of dimension d - 1 (keys (cloud << col_bits) | idx(sigma)), or null
-  const uint64_t* pmap_keys;
+  const uint64_t* pmap;
   uint64_t pmap_mask;
   // launch and scheduling parameters (rips_tuning_t)
   uint32_t chain_limit;            // additions a warp makes on one column before a block takes it
