@@ -48,7 +48,7 @@ def distances32(points: np.ndarray) -> np.ndarray:
 
 
 def critical_edge(d32: np.ndarray, index: int, dim: int) -> tuple[int, int]:
-    """Longest edge (a > b) of the simplex, ties -> smallest edge index, judged on
+    """Longest edge (a > b) of the simplex, ties -> smallest edge index, compared on
     the FP32 matrix the barcode was computed from."""
     v = simplex_vertices(index, dim)
     best = None
