@@ -1727,7 +1727,10 @@ __device__ bool block_merge_small(const RedState& s, unsigned char* raw, MergeRe
   return true;
 }
 
-constexpr uint32_t MID_MERGE = (uint32_t)(RED_SMEM_BYTES / 12);  // entries staged in shared memory at once
+// Entries of one chunk of a block merge: the staged ranges and their merged
+// order both live in the block's shared tile.
+constexpr uint32_t MID_MERGE = 1536;
+static_assert((size_t)MID_MERGE * 24 <= RED_SMEM_BYTES, "two chunk buffers fit the shared tile");
 
 // first position in the sorted keys k[0, len) whose key is >= x
 __device__ __forceinline__ uint32_t lower_bound_u64(const uint64_t* k, uint32_t len, uint64_t x) {
@@ -1740,20 +1743,24 @@ __device__ __forceinline__ uint32_t lower_bound_u64(const uint64_t* k, uint32_t 
   return lo;
 }
 
-// Merge the ranges [lo[r], hi[r]) of the request's runs (shared-memory arrays;
-// at most MID_MERGE entries together) and append the nonzero sums to (fk, fc)
-// from position `out`; returns how many were appended (the same in every
-// thread).  All keys and scaled coefficients of the ranges are staged in shared
-// memory; every entry finds its place in the merged order by binary searches in
-// the other ranges (equal keys ordered by run); the entry of the first run
-// holding a key takes the group's coefficient sum, the others coefficient 0;
-// that order goes to the scratch (tk, tc), from which a block scan packs the
-// nonzero entries.  Called by the whole block.
+// Merge the ranges [lo[r], hi[r]) of the request's runs (at most MID_MERGE
+// entries together) and append the nonzero sums to (fk, fc) from position
+// `out`; returns how many were appended (the same in every thread).  The ranges
+// are staged in shared memory as consecutive segments with scaled
+// coefficients, then merged two segments at a time, ceil(log2 n) rounds
+// between two buffers: every thread emits a fixed share of a round's output,
+// starting where a merge-path search on its first output puts it (equal keys:
+// the earlier segment first).  In the merged order the entries of one key are
+// adjacent (at most one per run); the first of each group takes the group's
+// coefficient sum, and a block scan packs the nonzero sums.  Called by the
+// whole block.
 __device__ uint32_t chunk_merge(MergeReq& q, unsigned char* raw, const uint32_t* lo, const uint32_t* hi, uint32_t n,
-                                uint32_t p, uint64_t* tk, uint32_t* tc, uint64_t* fk, uint32_t* fc, uint32_t out) {
+                                uint32_t p, uint64_t* fk, uint32_t* fc, uint32_t out) {
   const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   uint64_t* sk = (uint64_t*)raw;
-  uint32_t* sc = (uint32_t*)(raw + (size_t)MID_MERGE * 8);
+  uint64_t* dk = sk + MID_MERGE;
+  uint32_t* sc = (uint32_t*)(raw + (size_t)MID_MERGE * 16);
+  uint32_t* dc = sc + MID_MERGE;
   if (tid == 0) {
     uint32_t acc = 0;
     for (uint32_t i = 0; i < n; ++i) {
@@ -1773,35 +1780,58 @@ __device__ uint32_t chunk_merge(MergeReq& q, unsigned char* raw, const uint32_t*
     sc[e] = R.scale == 1 ? R.coef[i] : (uint32_t)(((uint64_t)R.coef[i] * R.scale) % p);
   }
   __syncthreads();
-  for (uint32_t e = tid; e < total; e += blockDim.x) {
-    uint32_t r = 0;
-    while (e >= q.roff[r + 1]) ++r;
-    const uint64_t k = sk[e];
-    uint32_t pos = e - q.roff[r], c = sc[e];
-    bool head = true;
-    for (uint32_t r2 = 0; r2 < n; ++r2) {
-      if (r2 == r) continue;
-      const uint32_t b = q.roff[r2], len = q.roff[r2 + 1] - b;
-      const uint32_t lb = lower_bound_u64(sk + b, len, k);
-      const bool eq = lb < len && sk[b + lb] == k;
-      if (r2 < r) {
-        pos += lb + (eq ? 1u : 0u);
-        head = head && !eq;
-      } else {
-        pos += lb;
-        if (eq) c = (c + sc[b + lb]) % p;
-      }
-    }
-    tk[pos] = k;
-    tc[pos] = head ? c : 0u;
-  }
-  __syncthreads();
-  // pack: thread t takes the entries [t * per, (t + 1) * per) of the merged order
   const uint32_t per = (total + blockDim.x - 1) / blockDim.x;
   const uint32_t e0 = tid * per < total ? tid * per : total;
   const uint32_t e1 = e0 + per < total ? e0 + per : total;
+  for (uint32_t nseg = n; nseg > 1; nseg = (nseg + 1) / 2) {
+    // segments 2g and 2g+1 become one; a last odd segment is copied
+    uint32_t e = e0, g = 0;
+    while (e < e1) {
+      while (q.roff[2 * g + 2 < nseg ? 2 * g + 2 : nseg] <= e) ++g;
+      const uint32_t xs = q.roff[2 * g];
+      const uint32_t xe = q.roff[2 * g + 1 < nseg ? 2 * g + 1 : nseg];
+      const uint32_t ye = q.roff[2 * g + 2 < nseg ? 2 * g + 2 : nseg];
+      const uint32_t a = xe - xs, b = ye - xe, dg = e - xs;
+      // i = entries of X among the pair's first dg outputs
+      uint32_t ilo = dg > b ? dg - b : 0u, ihi = dg < a ? dg : a;
+      while (ilo < ihi) {
+        const uint32_t mid = (ilo + ihi) >> 1;
+        if (sk[xs + mid] <= sk[xe + dg - mid - 1]) ilo = mid + 1;
+        else ihi = mid;
+      }
+      uint32_t i = ilo, j = dg - ilo;
+      const uint32_t stop = e1 < ye ? e1 : ye;
+      for (; e < stop; ++e) {
+        const bool take_x = j >= b || (i < a && sk[xs + i] <= sk[xe + j]);
+        const uint32_t src = take_x ? xs + i : xe + j;
+        dk[e] = sk[src];
+        dc[e] = sc[src];
+        if (take_x) ++i;
+        else ++j;
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {  // the merged pairs are the next round's segments
+      uint32_t m = 0;
+      for (uint32_t s2 = 0; s2 < nseg; s2 += 2) q.roff[m++] = q.roff[s2];
+      q.roff[m] = total;
+    }
+    uint64_t* tk = sk;
+    sk = dk;
+    dk = tk;
+    uint32_t* tc = sc;
+    sc = dc;
+    dc = tc;
+    __syncthreads();
+  }
+  // group sums at the first entry of each key, then pack the nonzero ones
   uint32_t cnt = 0;
-  for (uint32_t e = e0; e < e1; ++e) cnt += tc[e] != 0;
+  for (uint32_t e = e0; e < e1; ++e) {
+    if (e && sk[e - 1] == sk[e]) continue;
+    uint32_t c = sc[e];
+    for (uint32_t x = e + 1; x < total && sk[x] == sk[e]; ++x) c = (c + sc[x]) % p;
+    cnt += c != 0;
+  }
   uint32_t incl = cnt;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -1817,9 +1847,12 @@ __device__ uint32_t chunk_merge(MergeReq& q, unsigned char* raw, const uint32_t*
   }
   uint32_t o = out + base + incl - cnt;
   for (uint32_t e = e0; e < e1; ++e) {
-    if (tc[e]) {
-      fk[o] = tk[e];
-      fc[o] = tc[e];
+    if (e && sk[e - 1] == sk[e]) continue;
+    uint32_t c = sc[e];
+    for (uint32_t x = e + 1; x < total && sk[x] == sk[e]; ++x) c = (c + sc[x]) % p;
+    if (c) {
+      fk[o] = sk[e];
+      fc[o] = c;
       ++o;
     }
   }
@@ -1827,7 +1860,7 @@ __device__ uint32_t chunk_merge(MergeReq& q, unsigned char* raw, const uint32_t*
   return kept;
 }
 
-constexpr uint32_t MERGE_CHUNKS = 256;  // most chunks of one big merge
+constexpr uint32_t MERGE_CHUNKS = 4096;  // most chunks of one big merge
 
 // The request's runs merged in one pass into one run of scale 1 in q.d[0], in
 // chunks of at most MID_MERGE entries: splitters taken every S entries of the
@@ -1849,14 +1882,14 @@ __device__ int block_merge_chunked(const RedState& s, unsigned char* raw, MergeR
   uint32_t K = total <= MID_MERGE ? 1u : (lenL + S - 1) / S;
   if (K < 1) K = 1;
   if (K > MERGE_CHUNKS) return -1;
-  // arena: scratch for one chunk, the output, and the chunk boundaries
-  const unsigned long long want = (unsigned long long)MID_MERGE + total + (unsigned long long)K * n;
+  // arena: the output and the chunk boundaries
+  const unsigned long long want = (unsigned long long)total + (unsigned long long)K * n;
   if (tid == 0) block_reserve(s, q, want);
   __syncthreads();
   const unsigned long long off = q.off;
   if (off + want > s.r_cap) return 0;
   // bnd[c * n + r] = where run r enters chunk c + 1
-  uint32_t* bnd = s.r_coef + off + MID_MERGE + total;
+  uint32_t* bnd = s.r_coef + off + total;
   for (uint32_t t = tid; t < (K - 1) * n; t += blockDim.x) {
     const uint32_t c = t / n, r = t % n;
     const uint64_t sp = q.d[L].key[(c + 1) * S];
@@ -1875,10 +1908,8 @@ __device__ int block_merge_chunked(const RedState& s, unsigned char* raw, MergeR
   }
   __syncthreads();
   if (!fits) return -1;
-  uint64_t* tk = s.r_key + off;
-  uint32_t* tc = s.r_coef + off;
-  uint64_t* fk = s.r_key + off + MID_MERGE;
-  uint32_t* fc = s.r_coef + off + MID_MERGE;
+  uint64_t* fk = s.r_key + off;
+  uint32_t* fc = s.r_coef + off;
   __shared__ uint32_t clo[32], chi[32];
   uint32_t out = 0;
   for (uint32_t c = 0; c < K; ++c) {
@@ -1887,7 +1918,7 @@ __device__ int block_merge_chunked(const RedState& s, unsigned char* raw, MergeR
       chi[tid] = c + 1 < K ? bnd[c * n + tid] : q.d[tid].len;
     }
     __syncthreads();
-    out += chunk_merge(q, raw, clo, chi, n, p, tk, tc, fk, fc, out);
+    out += chunk_merge(q, raw, clo, chi, n, p, fk, fc, out);
   }
   if (tid == 0) {
     q.d[0] = RunDesc{fk, fc, out, 1};
