@@ -2,6 +2,8 @@
 // death, then birth simplex index.  Up to SMALL_BARS bars: one comparison sort
 // in shared memory.  Beyond that: three stable LSD radix sorts of a permutation
 // (least significant key first), then one gather.
+#include <atomic>
+
 #include "rips_internal.cuh"
 
 namespace rips {
@@ -89,15 +91,15 @@ cudaError_t launch_bar_order(rips_bar_t* bars, rips_bar_t* bars_alt, uint32_t nb
     uint32_t n2 = 2;
     while (n2 < nb) n2 <<= 1;
     const size_t smem = (size_t)n2 * 28;
-    static bool opted[64] = {};  // once per device
+    static std::atomic<bool> opted[64];  // once per device (any thread)
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64 || !opted[dev]) {
+    if (dev < 0 || dev >= 64 || !opted[dev].load(std::memory_order_acquire)) {
       e = cudaFuncSetAttribute(bar_order_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)(SMALL_BARS * 28));
       if (e != cudaSuccess) return e;
-      if (dev >= 0 && dev < 64) opted[dev] = true;
+      if (dev >= 0 && dev < 64) opted[dev].store(true, std::memory_order_release);
     }
     bar_order_small_kernel<<<1, 1024, smem, s>>>(bars, nb, n2, bars_alt);
     note_launch();

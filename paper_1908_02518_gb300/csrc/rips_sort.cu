@@ -9,6 +9,8 @@
 //       __match_any_sync, warps are ordered by a shared-memory prefix, so keys
 //       with equal digits keep their relative order (LSD correctness).
 
+#include <atomic>
+
 #include "rips_internal.cuh"
 
 namespace rips {
@@ -272,14 +274,14 @@ cudaError_t radix_sort_u64(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, u
     while (n2 < n) n2 <<= 1;
     const size_t smem = (size_t)n2 * 8;
     if (smem > 48 * 1024) {
-      static bool opted[64] = {};  // once per device
+      static std::atomic<bool> opted[64];  // once per device (any thread)
       int dev = 0;
       cudaError_t e = cudaGetDevice(&dev);
       if (e != cudaSuccess) return e;
-      if (dev < 0 || dev >= 64 || !opted[dev]) {
+      if (dev < 0 || dev >= 64 || !opted[dev].load(std::memory_order_acquire)) {
         e = cudaFuncSetAttribute(sort_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SMALL_SORT * 8));
         if (e != cudaSuccess) return e;
-        if (dev >= 0 && dev < 64) opted[dev] = true;
+        if (dev >= 0 && dev < 64) opted[dev].store(true, std::memory_order_release);
       }
     }
     sort_small_kernel<<<1, 1024, smem, s>>>(keys, n, n2);
