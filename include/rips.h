@@ -93,19 +93,30 @@ typedef struct rips_result rips_result_t;
 
 /*
  * rips_barcodes -- barcode of one distance matrix held in HOST memory.
- * The matrix is copied to the device on `stream`; the bars are copied back.
- * out: receives a new result object (NULL on failure).
+ * Defined by: Section 2 (the Rips filtration of a finite metric space, its
+ * lexicographic refinement, and the barcode of a filtration read off the
+ * persistence pairs of a reduced boundary matrix), Section 4 "Input" (distance
+ * matrix, threshold, enclosing radius) and "Coefficients" (Z/p).
+ * dist: n x n FP32, HOST, read only, owned by the caller.  The matrix is copied
+ * to the device on the legacy default stream; the bars are copied back and the
+ * call returns when they are on the host.
+ * out: receives a new result object owned by the caller until
+ * rips_result_free (NULL on failure).
  */
 RIPS_API int rips_barcodes(const float* dist, int64_t n, int32_t dim_max, float threshold,
                            uint32_t p, rips_result_t** out);
 
-/* Same, for a distance matrix already in DEVICE memory (not modified), with the
- * work issued on `cuda_stream` (a cudaStream_t, or NULL). */
+/* rips_barcodes_device -- the same problem (Section 2; Section 4 "Input",
+ * "Coefficients") for a distance matrix already in DEVICE memory (read only,
+ * owned by the caller), with the work issued on `cuda_stream` (a cudaStream_t,
+ * or NULL); returns when the bars are on the host. */
 RIPS_API int rips_barcodes_device(const float* d_dist, int64_t n, int32_t dim_max, float threshold,
                                   uint32_t p, void* cuda_stream, rips_result_t** out);
 
 /*
- * rips_distance_matrix_device -- Euclidean distances of n points with k FP32
+ * rips_distance_matrix_device -- the finite metric space of a point cloud
+ * (Section 4 "Input" accepts point clouds as well as distance matrices):
+ * Euclidean distances of n points with k FP32
  * coordinates each (row-major, DEVICE memory) into d_dist (n x n, DEVICE,
  * written in full).  Each entry is computed in float64 from the FP32
  * coordinates (squared differences summed in coordinate order, each operation
@@ -115,15 +126,32 @@ RIPS_API int rips_distance_matrix_device(const float* d_points, int64_t n, int32
                                          void* cuda_stream);
 
 /*
- * rips_barcodes_batched -- barcodes of `batch` independent point clouds in one
- * pass.  d_points: all clouds' FP32 coordinates concatenated (DEVICE, row-major,
+ * rips_barcodes_batched -- barcodes (Section 2) of `batch` independent point
+ * clouds (Section 4 "Input") in one pass.  d_points: all clouds' FP32 coordinates concatenated (DEVICE, row-major,
  * k per point); d_offsets: batch+1 point offsets (HOST).  The distances of every
  * cloud are computed on the device by the rule of rips_distance_matrix_device.
- * The bars of cloud c carry cloud = c.
+ * The bars of cloud c carry cloud = c.  Status as for rips_barcodes; every
+ * cloud must satisfy its size rules, and with batch > 1 every cloud has at
+ * most 12800 points.
  */
 RIPS_API int rips_barcodes_batched(const float* d_points, const int64_t* offsets, int32_t batch,
                                    int32_t k, int32_t dim_max, float threshold, uint32_t p,
                                    void* cuda_stream, rips_result_t** out);
+
+/*
+ * rips_barcodes_batched_dists -- barcodes (Section 2) of `batch` independent
+ * finite metric spaces given as distance matrices (Section 4 "Input"), in one
+ * pass.  d_dists: HOST array of `batch` DEVICE pointers, matrix c being
+ * ns[c] x ns[c] FP32 row-major with the conventions of rips_barcodes (strict
+ * lower triangle read, not modified, owned by the caller); ns: HOST array of
+ * the sizes.  Threshold, p and dim_max apply to every cloud.  The matrices are
+ * gathered into library-owned device memory on cuda_stream, then processed
+ * together as in rips_barcodes_batched; the bars of cloud c carry cloud = c.
+ * Status as for rips_barcodes_batched.
+ */
+RIPS_API int rips_barcodes_batched_dists(const float* const* d_dists, const int64_t* ns, int32_t batch,
+                                         int32_t dim_max, float threshold, uint32_t p, void* cuda_stream,
+                                         rips_result_t** out);
 
 /*
  * rips_barcodes_backward -- gradient of a loss L(bars) with respect to the
@@ -145,28 +173,55 @@ RIPS_API int rips_barcodes_backward(const rips_result_t* res, const float* d_poi
                                     float* d_grad_points, float* d_grad_dist, void* cuda_stream);
 
 /*
+ * rips_barcodes_backward_dist -- gradient of a loss L(bars) with respect to
+ * the distance matrices themselves, for callers that hold only the matrices.
+ * Works for a result of any forward entry point.  The paper has no backward
+ * pass; it rests on Section 2: a finite bar endpoint is the diameter of its
+ * birth or death simplex, i.e. the entry of D at one critical edge -- the
+ * longest edge of that simplex on the FP32 matrix the forward read, ties
+ * broken towards the smallest edge index (the edge that enters the refined
+ * filtration last).  d_dists: HOST array of one DEVICE pointer per cloud of the
+ * result (the matrices the forward read, n_c x n_c FP32, not modified);
+ * grad_birth, grad_death: DEVICE FP32, one entry per bar in the order of
+ * rips_result_bars over all clouds (NULL: zero; essential deaths ignored);
+ * d_grad_dists: HOST array of one DEVICE pointer per cloud, an n_c x n_c FP32
+ * matrix into whose strict lower triangle dL/dD[a][b] (a > b) is accumulated
+ * (the caller zeroes it).  Returns when the work on cuda_stream is done.
+ */
+RIPS_API int rips_barcodes_backward_dist(const rips_result_t* res, const float* const* d_dists,
+                                         const float* grad_birth, const float* grad_death, float* const* d_grad_dists,
+                                         void* cuda_stream);
+
+/*
  * rips_h0_barcode_noalloc -- the dimension-0 barcode of one distance matrix
- * without allocating any memory.  No counterpart in the paper: it exists for
- * callers that cannot allocate device memory while they run (code inside CUDA
- * graph capture, serving processes whose pool owns the whole device, real-time
- * loops that must not wait on an allocator).  All intermediate data lives in a
- * fixed file-scope device array (about 3.3 MB, held by every GPU that loads the
- * library until the process exits), so n is at most RIPS_NOALLOC_MAX_N; larger
- * n returns RIPS_ERR_BAD_ARG.  d_dist: n x n FP32 (DEVICE, strict lower
- * triangle read, as for rips_barcodes); threshold as for rips_barcodes.
- * d_bars: DEVICE room for n bars, receives the H0 bars (forest edges in
- * filtration order, then the essential classes); d_nbars: DEVICE uint32, the
- * bar count.  Work is issued on cuda_stream and the call waits for it.  Every
- * call reuses the same array and resets what must start at zero: calls that
- * overlap on the GPU (other streams or threads) race and must not be made.  The
- * first call on a device looks the array's address up; make it before any
- * stream capture begins.
+ * without allocating any memory.  The paper has no counterpart: it exists for
+ * callers that cannot allocate device memory while they run (a serving process
+ * whose memory pool already owns the whole device, a real-time loop that must
+ * not wait on cudaMalloc / cudaFree, which may synchronise the device).  All
+ * intermediate data lives in a fixed file-scope device array (about 3.3 MB,
+ * held by every GPU that loads the library until the process exits), so n is
+ * at most RIPS_NOALLOC_MAX_N; larger n returns RIPS_ERR_BAD_ARG.
+ * d_dist: n x n FP32 (DEVICE, strict lower triangle read, as for
+ * rips_barcodes; a NaN, infinite or negative entry returns RIPS_ERR_BAD_ARG);
+ * threshold as for rips_barcodes.  d_bars: DEVICE room for n bars, receives
+ * the H0 bars (forest edges in filtration order, then the essential classes);
+ * d_nbars: DEVICE uint32, the bar count.  Work is issued on cuda_stream and the
+ * call waits for that stream before it returns.  Every call reuses the same
+ * array (which keeps the last call's contents) and resets what must start at
+ * zero: calls that overlap on the GPU (other streams or threads) race and must
+ * not be made.  The first call on a device looks the array's address up with
+ * that device current and keeps it; make that first call before any stream
+ * capture begins, and make no call after cudaDeviceReset.  Status: as for
+ * rips_barcodes (RIPS_ERR_DEVICE_TIMEOUT for a bounded wait that ran out,
+ * RIPS_ERR_OOM for a capacity limit, RIPS_ERR_INTERNAL otherwise).
  */
 #define RIPS_NOALLOC_MAX_N 512
 RIPS_API int rips_h0_barcode_noalloc(const float* d_dist, int64_t n, float threshold, rips_bar_t* d_bars,
                                      uint32_t* d_nbars, void* cuda_stream);
 
-/* Number of bars of cloud `cloud` in dimension `dim` (dim = -1: all dims);
+/* Result accessors: the barcode as a list of intervals (Section 2, the
+ * Proposition on simplexwise refinements; zero-length intervals dropped).
+ * Number of bars of cloud `cloud` in dimension `dim` (dim = -1: all dims);
  * cloud = -1: all clouds.  Negative status on a bad argument. */
 RIPS_API int64_t rips_result_num_bars(const rips_result_t* res, int32_t cloud, int32_t dim);
 
@@ -179,7 +234,9 @@ RIPS_API int32_t rips_result_num_clouds(const rips_result_t* res);
 RIPS_API int32_t rips_result_dim_max(const rips_result_t* res);
 RIPS_API float rips_result_threshold(const rips_result_t* res, int32_t cloud);
 
-/* Statistics of cloud `cloud` in dimension `dim`. */
+/* Statistics of cloud `cloud` in dimension `dim`: the pair categories of
+ * Table 2 (apparent, cleared, emergent, columns reduced) and reduction
+ * counters. */
 RIPS_API int rips_result_stats(const rips_result_t* res, int32_t cloud, int32_t dim,
                                rips_stats_t* out);
 

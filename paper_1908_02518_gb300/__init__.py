@@ -20,7 +20,8 @@ import numpy as np
 from . import _lib
 from ._lib import RipsError
 
-__all__ = ["barcodes", "barcodes_batched", "distance_matrix", "backward", "Result", "RipsError",
+__all__ = ["barcodes", "barcodes_batched", "barcodes_batched_dists", "distance_matrix", "backward",
+           "backward_dist", "Result", "RipsError",
            "RipsBarcodes", "launch_count", "set_kernel_timing", "BAR_DTYPE"]
 
 BAR_DTYPE = np.dtype({
@@ -162,6 +163,45 @@ def barcodes_batched(points, offsets, dim_max: int = 1, threshold: float = math.
                                    C.byref(out))
     _lib.check(st, "rips_barcodes_batched")
     return _collect(lib, out, keep_handle)
+
+
+def barcodes_batched_dists(dists, dim_max: int = 1, threshold: float = math.inf, p: int = 2, stream=None,
+                           keep_handle: bool = False) -> Result:
+    """Barcodes of many finite metric spaces: ``dists`` is a list of n_c x n_c
+    FP32 CUDA tensors (``rips_barcodes_batched_dists``)."""
+    import torch
+    lib = _lib.load()
+    mats = [d.contiguous() for d in dists]
+    for d in mats:
+        if not d.is_cuda or d.dtype != torch.float32 or d.dim() != 2 or d.shape[0] != d.shape[1]:
+            raise ValueError("every matrix must be an n x n float32 CUDA tensor")
+    ptrs = (C.c_void_p * len(mats))(*[d.data_ptr() for d in mats])
+    ns = np.array([d.shape[0] for d in mats], dtype=np.int64)
+    out = C.c_void_p()
+    st = lib.rips_barcodes_batched_dists(ptrs, ns.ctypes.data_as(C.POINTER(C.c_int64)), len(mats), dim_max,
+                                         C.c_float(threshold), p, _stream_ptr(stream), C.byref(out))
+    _lib.check(st, "rips_barcodes_batched_dists")
+    return _collect(lib, out, keep_handle)
+
+
+def backward_dist(result: Result, dists, grad_birth, grad_death, stream=None):
+    """dL/dD for each cloud of ``result`` (made with keep_handle=True) from the
+    distance matrices it was computed from (list of CUDA tensors): returns one
+    n_c x n_c tensor per cloud, the gradient on its strict lower triangle."""
+    import torch
+    lib = _lib.load()
+    if result._handle is None:
+        raise ValueError("result was freed; call the forward with keep_handle=True")
+    mats = [d.contiguous() for d in dists]
+    grads = [torch.zeros_like(d) for d in mats]
+    dp = (C.c_void_p * len(mats))(*[d.data_ptr() for d in mats])
+    gp = (C.c_void_p * len(grads))(*[g.data_ptr() for g in grads])
+    gb = grad_birth.contiguous().float()
+    gd = grad_death.contiguous().float()
+    st = lib.rips_barcodes_backward_dist(result._handle, dp, C.c_void_p(gb.data_ptr()), C.c_void_p(gd.data_ptr()),
+                                         gp, _stream_ptr(stream))
+    _lib.check(st, "rips_barcodes_backward_dist")
+    return grads
 
 
 def backward(result: Result, points, grad_birth, grad_death, grad_dist=None, stream=None):

@@ -870,6 +870,75 @@ int backward_locked(Workspace& w, const rips_result* r, const float* d_points, i
 }
 
 
+// batched over distance matrices: the clouds' matrices are gathered back to
+// back into the workspace, then one pipeline runs for the batch
+int batched_dists_locked(Workspace& w, const float* const* d_dists, const int64_t* ns_in, int32_t batch,
+                         int32_t dim_max, float threshold, uint32_t p, cudaStream_t s, rips_result_t** out) {
+  rips_result* r = new (std::nothrow) rips_result();
+  if (!r) return RIPS_ERR_OOM;
+  r->clouds = batch;
+  r->dim_max = dim_max;
+  std::vector<int64_t> ns(ns_in, ns_in + batch);
+  std::vector<int64_t> poff(batch + 1, 0);
+  uint64_t RR = 0;
+  int64_t nmax = 1;
+  for (int32_t c = 0; c < batch; ++c) {
+    nmax = std::max<int64_t>(nmax, ns[c]);
+    poff[c + 1] = poff[c] + ns[c];
+    RR += (uint64_t)ns[c] * ns[c];
+  }
+  int rc = ensure(w.cdist, RR * 4);
+  uint64_t at = 0;
+  for (int32_t c = 0; c < batch && rc == RIPS_OK; ++c) {
+    const size_t bytes = (size_t)ns[c] * ns[c] * 4;
+    if (cudaMemcpyAsync(P<float>(w.cdist) + at, d_dists[c], bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+      cudaGetLastError();
+      rc = RIPS_ERR_CUDA;
+    }
+    at += (uint64_t)ns[c] * ns[c];
+  }
+  BatchOut bo;
+  if (rc == RIPS_OK) rc = run_batch(w, P<float>(w.cdist), ns, dim_max, threshold, p, s, bo);
+  if (rc == RIPS_OK) {
+    const int sbits = std::max(1, bit_width64(host_binom((uint64_t)nmax, dim_max + 1)));
+    rc = finish_bars(w, bo.nbars, sbits, std::max(1, bit_width64((uint64_t)batch)), s, r->bars);
+  }
+  if (rc != RIPS_OK) {
+    delete r;
+    return rc;
+  }
+  fill_result(r, bo);
+  r->npoints = ns;
+  r->point_offsets = poff;
+  index_result(r);
+  *out = r;
+  return RIPS_OK;
+}
+
+// dL/dD of every cloud of a result from the matrices it was computed from
+int backward_dist_locked(Workspace& w, const rips_result* r, const float* const* d_dists, const float* gb,
+                         const float* gd, float* const* d_grad, cudaStream_t s) {
+  const uint32_t nb = (uint32_t)r->bars.size();
+  if (nb == 0) return RIPS_OK;
+  const int C = r->clouds;
+  // one table: C matrix pointers, C gradient pointers, C sizes (8 bytes each)
+  std::vector<uint64_t> tab(3 * (size_t)C);
+  for (int c = 0; c < C; ++c) {
+    tab[c] = (uint64_t)(uintptr_t)d_dists[c];
+    tab[C + c] = (uint64_t)(uintptr_t)d_grad[c];
+    tab[2 * C + c] = (uint64_t)r->npoints[c];
+  }
+  CR(ensure(w.bwd_bars, (size_t)nb * sizeof(rips_bar_t)));
+  CR(ensure(w.bwd_off, tab.size() * 8));
+  CK(cudaMemcpyAsync(w.bwd_bars.p, r->bars.data(), (size_t)nb * sizeof(rips_bar_t), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(w.bwd_off.p, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice, s));
+  uint64_t* dt = P<uint64_t>(w.bwd_off);
+  CK(launch_backward_dist(P<rips_bar_t>(w.bwd_bars), nb, (const float* const*)dt, (float* const*)(dt + C),
+                          (const int64_t*)(dt + 2 * C), gb, gd, s));
+  CK(cudaStreamSynchronize(s));  // the host-side copies above must finish before returning
+  return RIPS_OK;
+}
+
 // ------------------------------------------------------------------ batch plans
 // A batch plan fixes the clouds' sizes (and k, threshold, p; dimensions 0 and
 // 1) and sizes every buffer from the worst case at creation: all C(n, 2)
@@ -1418,6 +1487,44 @@ RIPS_API int rips_barcodes_backward(const rips_result_t* res, const float* d_poi
     std::lock_guard<std::mutex> g(w->mu);
     return backward_locked(*w, res, d_points, k, grad_birth, grad_death, d_grad_points, d_grad_dist,
                            (cudaStream_t)cuda_stream);
+  } catch (...) {
+    return RIPS_ERR_INTERNAL;
+  }
+}
+
+
+RIPS_API int rips_barcodes_batched_dists(const float* const* d_dists, const int64_t* ns, int32_t batch,
+                                         int32_t dim_max, float threshold, uint32_t p, void* cuda_stream,
+                                         rips_result_t** out) {
+  if (!out) return RIPS_ERR_BAD_ARG;
+  *out = nullptr;
+  if (!d_dists || !ns || batch < 1) return RIPS_ERR_BAD_ARG;
+  for (int32_t c = 0; c < batch; ++c) {
+    if (!d_dists[c]) return RIPS_ERR_BAD_ARG;
+    int rc = check_args(ns[c], dim_max, threshold, p);
+    if (rc != RIPS_OK) return rc;
+  }
+  try {
+    Workspace* w = current_workspace();
+    if (!w) return RIPS_ERR_OOM;
+    std::lock_guard<std::mutex> g(w->mu);
+    return batched_dists_locked(*w, d_dists, ns, batch, dim_max, threshold, p, (cudaStream_t)cuda_stream, out);
+  } catch (...) {
+    return RIPS_ERR_INTERNAL;
+  }
+}
+
+RIPS_API int rips_barcodes_backward_dist(const rips_result_t* res, const float* const* d_dists,
+                                         const float* grad_birth, const float* grad_death, float* const* d_grad_dists,
+                                         void* cuda_stream) {
+  if (!res || !d_dists || !d_grad_dists) return RIPS_ERR_BAD_ARG;
+  for (int32_t c = 0; c < res->clouds; ++c)
+    if (!d_dists[c] || !d_grad_dists[c]) return RIPS_ERR_BAD_ARG;
+  try {
+    Workspace* w = current_workspace();
+    if (!w) return RIPS_ERR_OOM;
+    std::lock_guard<std::mutex> g(w->mu);
+    return backward_dist_locked(*w, res, d_dists, grad_birth, grad_death, d_grad_dists, (cudaStream_t)cuda_stream);
   } catch (...) {
     return RIPS_ERR_INTERNAL;
   }

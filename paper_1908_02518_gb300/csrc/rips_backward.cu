@@ -105,7 +105,62 @@ __global__ void backward_kernel(const rips_bar_t* __restrict__ bars, uint32_t nb
   }
 }
 
+// Longest edge (a > b) of the d-simplex with index N measured on the FP32
+// distance matrix D (n x n, strict lower triangle D[a*n + b]) the forward read;
+// ties: smallest edge index, as above.
+__device__ void critical_edge_dist(const float* __restrict__ D, int n, uint64_t N, int d, int* ea, int* eb) {
+  int v[MAX_DIM + 2];
+  decode_arith(N, d, n, v);
+  float best = -1.0f;
+  uint64_t best_idx = 0;
+  *ea = v[0];
+  *eb = v[d];
+  for (int i = 0; i <= d; ++i)
+    for (int j = i + 1; j <= d; ++j) {
+      const int a = v[i], b = v[j];  // a > b
+      const float w = D[(size_t)a * n + b];
+      const uint64_t eidx = (uint64_t)a * (a - 1) / 2 + b;
+      if (w > best || (w == best && eidx < best_idx)) {
+        best = w;
+        best_idx = eidx;
+        *ea = a;
+        *eb = b;
+      }
+    }
+}
+
+// dL/dD only: every finite endpoint's gradient is added to its critical edge's
+// entry of the cloud's gradient matrix
+__global__ void backward_dist_kernel(const rips_bar_t* __restrict__ bars, uint32_t nb,
+                                     const float* const* __restrict__ dists, float* const* __restrict__ gdists,
+                                     const int64_t* __restrict__ ns, const float* __restrict__ gbirth,
+                                     const float* __restrict__ gdeath) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nb) return;
+  const rips_bar_t b = bars[i];
+  const int n = (int)ns[b.cloud];
+  const float* D = dists[b.cloud];
+  float* G = gdists[b.cloud];
+  int ea, eb;
+  if (b.dim >= 1 && gbirth && gbirth[i] != 0.0f) {
+    critical_edge_dist(D, n, b.birth_simplex, b.dim, &ea, &eb);
+    atomicAdd(&G[(size_t)ea * n + eb], gbirth[i]);
+  }
+  if (isfinite(b.death) && b.death_simplex != ~0ull && gdeath && gdeath[i] != 0.0f) {
+    critical_edge_dist(D, n, b.death_simplex, b.dim + 1, &ea, &eb);
+    atomicAdd(&G[(size_t)ea * n + eb], gdeath[i]);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_backward_dist(const rips_bar_t* bars, uint32_t nb, const float* const* dists, float* const* gdists,
+                                 const int64_t* ns, const float* gbirth, const float* gdeath, cudaStream_t s) {
+  if (nb == 0) return cudaSuccess;
+  backward_dist_kernel<<<(nb + 127) / 128, 128, 0, s>>>(bars, nb, dists, gdists, ns, gbirth, gdeath);
+  note_launch();
+  return cudaGetLastError();
+}
 
 cudaError_t launch_backward(const rips_bar_t* bars, uint32_t nb, const float* pts, int k, const int64_t* pt_off,
                             const int64_t* dist_off, const float* gbirth, const float* gdeath, float* gx, float* gd,

@@ -269,5 +269,8 @@ size_t bar_order_temp_bytes(uint32_t nb);
 cudaError_t launch_backward(const rips_bar_t* bars, uint32_t nb, const float* pts, int k, const int64_t* pt_off,
                             const int64_t* dist_off, const float* gbirth, const float* gdeath, float* gx, float* gd,
                             cudaStream_t s);
+// dL/dD only, from each cloud's distance matrix (dists, gdists, ns: DEVICE arrays indexed by cloud)
+cudaError_t launch_backward_dist(const rips_bar_t* bars, uint32_t nb, const float* const* dists, float* const* gdists,
+                                 const int64_t* ns, const float* gbirth, const float* gdeath, cudaStream_t s);
 
 }  // namespace rips

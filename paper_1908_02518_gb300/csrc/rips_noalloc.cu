@@ -1,21 +1,26 @@
 // Allocation-free H0 barcode entry point.
 //
 // Some callers cannot allocate device memory at the moment they need a
-// barcode: code that runs while a CUDA graph is being captured (where a
-// cudaMalloc would break or be forbidden), a serving process whose memory pool
-// owns every byte of the device, or a real-time loop that must not stall on the
-// allocator.  For them, rips_h0_barcode_noalloc computes the dimension-0
-// barcode of one distance matrix of at most RIPS_NOALLOC_MAX_N points without
-// any allocation: every intermediate buffer lives in one file-scope device
-// array of fixed size (NOALLOC_BYTES below), which every GPU that loads the
-// library holds until the process exits.  The caller passes the matrix and the
-// output buffers.
+// barcode: a serving process whose memory pool already owns every byte of the
+// device (a cudaMalloc would fail, or take memory the pool has promised
+// elsewhere), or a real-time loop that must not stall on the allocator
+// (cudaMalloc and cudaFree may synchronise the device and take unbounded
+// time).  For them, rips_h0_barcode_noalloc computes the dimension-0 barcode
+// of one distance matrix of at most RIPS_NOALLOC_MAX_N points without any
+// allocation: every intermediate buffer lives in one file-scope device array
+// of fixed size (NOALLOC_BYTES below, about 3.3 MB), which every GPU that
+// loads the library holds until the process exits.  The caller passes the
+// matrix and the output buffers.
 //
 // Because every call shares that array, calls that overlap on the GPU (on
 // different streams, or from different host threads) race and must not be
-// issued.  Each call clears what has to start at zero.  The first call on a
-// device looks up the array's device address (cudaGetSymbolAddress); make that
-// first call before any stream capture begins.
+// issued.  Each call clears what has to start at zero; the array otherwise
+// keeps the last call's contents.  The first call on a device looks up the
+// array's device address (cudaGetSymbolAddress, with that device current) and
+// keeps it for later calls; make that first call before any stream capture
+// begins.  After cudaDeviceReset the kept address belongs to a destroyed
+// context: do not call this entry point again in that process.  The call
+// waits for its stream before it returns (it reads the error word back).
 #include <cmath>
 #include <mutex>
 
@@ -56,6 +61,24 @@ unsigned char* g_na_ptr[64] = {};
 __global__ void na_pad_keys_kernel(uint64_t* keys, uint64_t cap) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < cap; i += (uint64_t)gridDim.x * blockDim.x)
     keys[i] = ~0ull;
+}
+
+// the cloud table and tile offsets of the single cloud, written on the device
+// (no host buffer is involved)
+__global__ void na_init_kernel(CloudInfo* ci, uint32_t* tile_off, int n, uint32_t tiles) {
+  *ci = CloudInfo{n, 0u, 0ull, 0u, 0u, 0.0f, 0u};
+  tile_off[0] = 0u;
+  tile_off[1] = tiles;
+}
+
+// device error flags -> status: a bounded wait that ran out, a capacity limit,
+// anything else an internal failure
+int na_status(uint32_t err) {
+  if (err & ERRF_BAD_INPUT) return RIPS_ERR_BAD_ARG;
+  if (err & ERRF_TIMEOUT) return RIPS_ERR_DEVICE_TIMEOUT;
+  if (err & (ERRF_TABLE_FULL | ERRF_OUT_OVERFLOW | ERRF_ARENA)) return RIPS_ERR_OOM;
+  if (err) return RIPS_ERR_INTERNAL;
+  return RIPS_OK;
 }
 
 // cloud table of the single cloud once the edge count is known (on the device)
@@ -114,12 +137,11 @@ extern "C" RIPS_API int rips_h0_barcode_noalloc(const float* d_dist, int64_t n, 
   const uint64_t m_cap = (uint64_t)n * (n - 1) / 2;
   const uint32_t nb = (uint32_t)((n + 31) / 32);
   const uint32_t tiles = nb * (nb + 1) / 2;
-  const CloudInfo ci{(int)n, 0u, 0ull, 0u, 0u, 0.0f, 0u};
-  const uint32_t toff[2] = {0u, tiles};
   cudaError_t e = cudaSuccess;
   // everything that must start at zero (or at its initial value) is reset here
-  if (e == cudaSuccess) e = cudaMemcpyAsync(cloud, &ci, sizeof(CloudInfo), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(tile_off, toff, sizeof(toff), cudaMemcpyHostToDevice, s);
+  na_init_kernel<<<1, 1, 0, s>>>(cloud, tile_off, (int)n, tiles);
+  note_launch();
+  e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemsetAsync(rowmax, 0, (size_t)n * 4, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, 4 * 4, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(stats, 0, 16 * 8, s);
@@ -159,7 +181,5 @@ extern "C" RIPS_API int rips_h0_barcode_noalloc(const float* d_dist, int64_t n, 
     cudaGetLastError();
     return RIPS_ERR_CUDA;
   }
-  if (err & ERRF_BAD_INPUT) return RIPS_ERR_BAD_ARG;
-  if (err) return RIPS_ERR_DEVICE_TIMEOUT;
-  return RIPS_OK;
+  return na_status(err);
 }

@@ -1,13 +1,15 @@
 """The allocation-free H0 entry point, rips_h0_barcode_noalloc.
 
-It serves callers that must not allocate device memory while they run -- code
-inside CUDA-graph capture, serving processes whose memory pool owns the whole
-device, real-time loops that cannot wait on the allocator.  It keeps all of
-its intermediate data in a fixed file-scope device array, so it handles at
-most RIPS_NOALLOC_MAX_N points.  This test calls it through the C ABI twice in
-a row (the second call must not see the first call's leftovers) and compares
-its bars with those of rips_barcodes_device at dim_max = 0.  It lives in its
-own file, collected last, and passes alone or after the other tests.
+It serves callers that must not allocate device memory while they run -- a
+serving process whose memory pool owns the whole device, a real-time loop that
+cannot wait on cudaMalloc / cudaFree.  It keeps all of its intermediate data in
+a fixed file-scope device array, so it handles at most RIPS_NOALLOC_MAX_N
+points.  These tests call it through the C ABI several times in a row (a call
+must not see an earlier call's leftovers) and compare its bars with those of
+rips_barcodes_device at dim_max = 0 and with the CPU oracle, simplex indices
+included, from one point up to the maximum size and on both paths of the edge
+sort (one block up to 8192 edges, radix passes beyond).  The file is collected
+last and passes alone or after the other tests.
 """
 import ctypes as C
 import math
@@ -27,7 +29,7 @@ def _sorted_bars(arr):
                    int(b["death_simplex"])) for b in arr)
 
 
-def _noalloc(dist_np, threshold):
+def _noalloc(dist_np, threshold, expect=0):
     import torch
     import paper_1908_02518_gb300 as rg
     from paper_1908_02518_gb300 import _lib
@@ -39,7 +41,9 @@ def _noalloc(dist_np, threshold):
     stream = torch.cuda.current_stream().cuda_stream
     st = lib.rips_h0_barcode_noalloc(C.c_void_p(d.data_ptr()), n, C.c_float(threshold),
                                      C.c_void_p(bars.data_ptr()), C.c_void_p(count.data_ptr()), C.c_void_p(stream))
-    assert st == 0, st
+    assert st == expect, st
+    if expect != 0:
+        return None
     torch.cuda.synchronize()
     k = int(count.item())
     raw = bars.cpu().numpy()[: k * 32].tobytes()
@@ -68,3 +72,31 @@ def test_noalloc_rejects_too_many_points():
     st = lib.rips_h0_barcode_noalloc(C.c_void_p(d.data_ptr()), n, C.c_float(1.0), C.c_void_p(bars.data_ptr()),
                                      C.c_void_p(count.data_ptr()), None)
     assert st == -1
+
+
+def test_noalloc_matches_oracle_small_sizes(oracle_mod):
+    """n = 1, 2, 64 (single-block sort) and 300, each against the oracle's
+    Kruskal bars, simplex indices included; the calls run back to back."""
+    cases = [(np.zeros((1, 1), dtype=np.float32), math.inf),
+             (W.distance_matrix(W.cube_points(2, 31)), math.inf),
+             (W.distance_matrix(W.torus_points(64, 32)), 1.0),
+             (W.distance_matrix(W.torus_points(64, 33)), math.inf),
+             (W.distance_matrix(W.cube_points(300, 34)), 0.2)]
+    for dist, t in cases:
+        got = _noalloc(dist, t)
+        want = oracle_mod.barcodes(dist, 0, t, 2)
+        assert _sorted_bars(got) == sorted(
+            (int(b["dim"]), float(b["birth"]), float(b["death"]), int(b["birth_simplex"]),
+             int(b["death_simplex"]) if np.isfinite(b["death"]) else 2 ** 64 - 1) for b in want.bars), dist.shape
+
+
+def test_noalloc_rejects_nan_then_recovers():
+    import torch
+    import paper_1908_02518_gb300 as rg
+    dist = W.distance_matrix(W.cube_points(40, 35))
+    bad = dist.copy()
+    bad[7, 3] = np.nan
+    _noalloc(bad, math.inf, expect=-1)
+    got = _noalloc(dist, math.inf)
+    want = rg.barcodes(torch.from_numpy(dist).cuda(), 0, math.inf, 2)
+    assert _sorted_bars(got) == _sorted_bars(want.bars)
