@@ -1,14 +1,17 @@
 """Benchmark: Vietoris–Rips barcodes on one GB300 (or N replicas under torchrun).
 
-Workload: 1000 points on a noisy 2-torus in R^3 (major radius 2, minor radius 1,
-sigma 0.02), FP32 distance matrix, threshold 1.0, barcodes H0-H2 over Z/2.
-A step is one full barcode computation (prologue, H0, and for d = 1, 2:
-enumeration, apparent-pair test, sort, reduction, readout) on the distance
-matrix already resident in HBM.  The unit is simplices: the number of
-simplices of dimension 0..2 with diameter <= threshold.
+Workload (default, the largest single-GPU configuration): 4096 Haar-random
+rotations of R^3 flattened to points of R^9, FP32 distance matrix, threshold
+1.4, barcodes H0-H2 over Z/2.  A step is one full barcode computation
+(prologue, H0, and for d = 1, 2: enumeration, apparent-pair test, sort,
+reduction, readout) on the distance matrix already resident in HBM.  The unit
+is simplices: the number of simplices of dimension 0..2 with diameter <=
+threshold.  The same line carries the batched forward+backward comparison
+(256 ragged clouds, one batched call against a per-cloud loop).
 
 Prints one JSON line.  ``--impl reference`` times the CPU oracle instead (the
-reference arm: a plain CPU implementation of the method, see oracle/).
+reference arm: a plain CPU implementation of the method, see oracle/) on a
+bounded sample of the workload.
 """
 from __future__ import annotations
 
@@ -27,7 +30,12 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "torus1000"
+WORKLOAD = "so3_4096"
+# Bounded samples of each workload for the CPU oracle (baseline and reference
+# arm): the first m points of the workload's matrix, same threshold and
+# dimensions.  The oracle needs about 1,100 s for all 4096 points of so3_4096;
+# its first 1536 points take a few seconds.
+ORACLE_SAMPLE_POINTS = {"so3_4096": 1536, "s3_192": 128}
 L2_FLUSH_BYTES = 256 << 20  # larger than the 129 MB L2
 
 
@@ -43,7 +51,9 @@ def parse():
                     help="warm-up calls then exactly one barcode call, for ncu launch lists and captures")
     ap.add_argument("--dim-max", type=int, default=None, help="override the workload's top dimension")
     ap.add_argument("--batched", action="store_true",
-                    help="256 ragged clouds: batched forward+backward against a per-cloud loop of the same path")
+                    help="only the batched line: 256 ragged clouds, batched forward+backward against a per-cloud loop")
+    ap.add_argument("--no-batched", action="store_true", help="leave the batched comparison out of the main line")
+    ap.add_argument("--e2e-reps", type=int, default=3, help="end-to-end calls timed through the C ABI")
     return ap.parse_args()
 
 
@@ -171,8 +181,9 @@ def measured_traffic(kernel_class: str, workload: str):
 
 def kernel_roofline(name, km, stats, n, peak, peak_kind):
     """HBM roofline of one kernel class: algorithmic bytes per launch (the
-    per-unit figures in the design doc times the units one launch processes) over the
-    class's average launch time, both from the CUDA-event kernel timing."""
+    bytes each unit of work must move, listed per kernel below, times the units
+    one launch processes) over the class's average launch time, both from the
+    CUDA-event kernel timing."""
     if name not in km or km[name][0] <= 0:
         return None
     launches = max(km[name][1], 1)
@@ -197,11 +208,14 @@ def kernel_roofline(name, km, stats, n, peak, peak_kind):
             "algorithmic_bytes": algo, "launches_per_step": launches}
 
 
-def run_batched(args):
+def measure_batched(args, full: bool):
     """Forward + backward of loss = sum over H1 bars of (death - birth)^2 over
     the 256 ragged clouds (64..512 points: circles, tori, cubes): one batched
     call against a loop of the same GPU path called per cloud, both timed with
-    CUDA events, inputs resident on the device."""
+    CUDA events, inputs resident on the device.  With ``full`` the forward alone
+    and a CUDA-graph replay of a batch plan are timed too.  Returns the
+    measurements (rank 0) and, for the CPU-reference check, the gradient of a
+    few small clouds."""
     import torch
     import paper_1908_02518_gb300 as rg
     from paper_1908_02518_gb300 import workloads as W
@@ -241,22 +255,25 @@ def run_batched(args):
             out.append(a.elapsed_time(b))
         return statistics.median(out), r
 
-    for _ in range(max(args.warmup, 1)):
+    for _ in range(max(min(args.warmup, 3), 1)):
         step(pts, offsets)
-    t_batch, (gx, loss, units) = timed(lambda: step(pts, offsets), max(args.steps // 4, 3))
+    t_batch, (gx, loss, units) = timed(lambda: step(pts, offsets), 3)
+    extra = {}
+    if full:
+        # the same forward as one CUDA-graph replay of a batch plan (sizes fixed in advance)
+        plan = rg.BatchPlan(offsets, pts.shape[1])
+        graph = plan.capture(pts)
 
-    # the same forward as one CUDA-graph replay of a batch plan (sizes fixed in advance)
-    plan = rg.BatchPlan(offsets, pts.shape[1])
-    graph = plan.capture(pts)
-
-    def replay():
-        graph.replay()
-        return plan.result()
-    t_graph_fwd, gres = timed(replay, max(args.steps // 4, 3))
-    t_fwd, fres = timed(lambda: rg.barcodes_batched(pts, offsets, 1), max(args.steps // 4, 3))
-    graph_same = sorted(map(tuple, gres.bars[["cloud", "dim", "birth", "death"]].tolist())) == \
-        sorted(map(tuple, fres.bars[["cloud", "dim", "birth", "death"]].tolist()))
-    plan.free()
+        def replay():
+            graph.replay()
+            return plan.result()
+        t_graph_fwd, gres = timed(replay, 3)
+        t_fwd, fres = timed(lambda: rg.barcodes_batched(pts, offsets, 1), 3)
+        graph_same = sorted(map(tuple, gres.bars[["cloud", "dim", "birth", "death"]].tolist())) == \
+            sorted(map(tuple, fres.bars[["cloud", "dim", "birth", "death"]].tolist()))
+        plan.free()
+        extra = {"forward_ms": max_over_ranks(t_fwd), "forward_graph_replay_ms": max_over_ranks(t_graph_fwd),
+                 "graph_bars_equal": graph_same}
 
     def loop():
         gs, ls, us = [], 0.0, 0
@@ -266,35 +283,76 @@ def run_batched(args):
             ls += l_
             us += u
         return torch.cat(gs), ls, us
-    loop()
-    t_loop, (gl, loss_l, units_l) = timed(loop, 3)
+    # warm the per-cloud path on the largest cloud (workspace sizes), then time the whole loop once
+    big = int(np.argmax(sizes))
+    step(dev_clouds[big], np.array([0, sizes[big]], dtype=np.int64))
+    t_loop, (gl, loss_l, units_l) = timed(loop, 1)
     t_batch_job, t_loop_job = max_over_ranks(t_batch), max_over_ranks(t_loop)
     units_job = sum_over_ranks(units)
     # the backward scatter adds with float atomics, so the order of additions
     # (and the last bits) differ between the two; compare within 1e-4 relative
     gdiff = float((gx - gl).abs().max())
     gscale = max(float(gl.abs().max()), 1e-6)
+    # small clouds kept for the CPU-reference gradient check (cpu_baseline leg)
+    sample = [i for i, n in enumerate(sizes) if n <= 160][:4]
+    kept = {i: (clouds[i], gx[offsets[i]:offsets[i + 1]].double().cpu().numpy()) for i in sample}
+    out = {"batch_fwd_bwd_ms": t_batch_job, "per_cloud_loop_ms": t_loop_job, "speedup": t_loop_job / t_batch_job,
+           "clouds_on_rank0": len(clouds), "points_on_rank0": int(offsets[-1]), "simplices": units_job,
+           "simplices_per_s": whole_job_rate(units_job, t_batch_job), "loss_rank0": loss,
+           "loss_close_to_loop": math.isclose(loss, loss_l, rel_tol=1e-9),
+           "grad_max_rel_diff_to_loop": gdiff / gscale, "grad_within_1e-4_of_loop": gdiff <= 1e-4 * gscale,
+           "workload": "batch256", "dim_max": 1, "p": 2}
+    out.update(extra)
+    return out, kept
+
+
+def batched_cpu_check(kept) -> dict:
+    """The batched GPU gradient of a few small clouds against the CPU reference
+    gradient (oracle pairs, float64), relative to its largest entry."""
+    import oracle
+    from oracle import gradients as G
+    worst = 0.0
+    for i, (pts, g) in kept.items():
+        d32 = G.distances32(pts)
+        bars = oracle.barcodes(d32, 1).dim(1)
+        bars = bars[np.isfinite(bars["death"])]
+        diff = bars["death"].astype(np.float64) - bars["birth"].astype(np.float64)
+        ref = G.bar_gradient(pts, bars, -2 * diff, 2 * diff)
+        worst = max(worst, float(np.abs(g - ref).max()) / max(float(np.abs(ref).max()), 1e-6))
+    return {"clouds": sorted(kept), "max_rel_diff": worst, "within_1e-4": worst <= 1e-4}
+
+
+def run_batched(args):
+    """The batched comparison as its own JSON line."""
+    world, rank, _ = dist_env()
+    res, kept = measure_batched(args, full=True)
     if rank != 0:
         return 0
-    print(json.dumps({"metric": "batched_forward_backward_ms", "value": t_batch_job, "unit": "ms",
-                      "higher_is_better": False, "n_gpus": world, "per_cloud_loop_ms": t_loop_job,
-                      "speedup": t_loop_job / t_batch_job, "forward_ms": max_over_ranks(t_fwd),
-                      "forward_graph_replay_ms": max_over_ranks(t_graph_fwd), "graph_bars_equal": graph_same,
-                      "clouds_on_rank0": len(clouds),
-                      "points_on_rank0": int(offsets[-1]), "simplices": units_job,
-                      "simplices_per_s": whole_job_rate(units_job, t_batch_job), "loss_rank0": loss,
-                      "loss_close_to_loop": math.isclose(loss, loss_l, rel_tol=1e-9), "grad_max_rel_diff_to_loop": gdiff / gscale,
-                      "grad_within_1e-4": gdiff <= 1e-4 * gscale, "dtype": "f32 coordinates; integer ranks",
-                      "data": "synthetic", "config": {"workload": "batch256", "dim_max": 1, "p": 2}}))
+    res["cpu_reference_grad_check"] = batched_cpu_check(kept)
+    line = {"metric": "batched_forward_backward_ms", "value": res.pop("batch_fwd_bwd_ms"), "unit": "ms",
+            "higher_is_better": False, "n_gpus": world, "dtype": "f32 coordinates; integer ranks",
+            "data": "synthetic", "config": {"workload": "batch256", "dim_max": 1, "p": 2}}
+    line.update(res)
+    print(json.dumps(line))
     return 0
+
+
+def oracle_sample(w):
+    """(matrix, description) of the bounded sample the CPU oracle runs on."""
+    m = ORACLE_SAMPLE_POINTS.get(w.name)
+    if m is None or m >= w.n:
+        return w.dist, f"the full {w.name} workload"
+    return (np.ascontiguousarray(w.dist[:m, :m]),
+            f"the first {m} of the {w.n} points of {w.name} (same matrix entries, threshold {w.threshold}, "
+            f"H0-H{w.dim_max}, Z/{w.p})")
 
 
 def cpu_baseline(w, budget_s=12.0):
     """The oracle as it stands, single-threaded on the host, repeated on the
-    full workload until about budget_s seconds of CPU work."""
+    bounded sample until about budget_s seconds of CPU work."""
     import oracle
     oracle.build()
-    d = w.dist
+    d, what = oracle_sample(w)
     t0 = time.perf_counter()
     runs = 0
     units = 0
@@ -306,7 +364,7 @@ def cpu_baseline(w, budget_s=12.0):
             break
     el = time.perf_counter() - t0
     return {"value": units / el, "unit": "simplices/s", "cores": 1, "kind": "oracle",
-            "sample": f"{runs} full runs of the {w.name} workload (cohomology oracle, {el:.1f} s)"}
+            "sample": f"{runs} runs on {what} (cohomology oracle, {el:.1f} s)"}
 
 
 def workload_config(w, world: int) -> dict:
@@ -323,13 +381,14 @@ def run_reference(args):
     w = load_workload(args.workload)
     import oracle
     oracle.build()
+    d, what = oracle_sample(w)
     units = None
     for _ in range(args.warmup):
-        oracle.barcodes(w.dist, w.dim_max, w.threshold, w.p)
+        oracle.barcodes(d, w.dim_max, w.threshold, w.p)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        r = oracle.barcodes(w.dist, w.dim_max, w.threshold, w.p)
+        r = oracle.barcodes(d, w.dim_max, w.threshold, w.p)
         times.append(time.perf_counter() - t0)
         units = sum(s["simplices"] for s in r.stats)
     tot = sum(times)
@@ -339,7 +398,7 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": workload_config(w, world),
             "cpu_baseline": {"value": val, "unit": "simplices/s", "cores": 1, "kind": "oracle",
-                             "sample": f"the full {w.name} workload per step"},
+                             "sample": f"{what} per step"},
             "e2e": {"value": val, "unit": "simplices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -419,7 +478,7 @@ def main():
     # dominant kernel class, timed live with events on the call's stream
     rg.set_kernel_timing(True)
     km = {}
-    kr = 3
+    kr = 3 if ms_per_step < 1000.0 else 1
     for _ in range(kr):
         flush.zero_()
         r = rg.barcodes(dev_d, w.dim_max, w.threshold, w.p)
@@ -448,13 +507,13 @@ def main():
     host = pinned.numpy()
     e2e_t = []
     nbars = 0
-    for k in range(max(3, args.steps // 2) + 2):
+    for k in range(max(1, args.e2e_reps) + 1):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         r = rg.barcodes(host, w.dim_max, w.threshold, w.p)
         t1 = time.perf_counter()
-        if k >= 2:
+        if k >= 1:
             e2e_t.append(t1 - t0)
         nbars = len(r.bars)
     e2e_s = max_over_ranks(sum(e2e_t) / len(e2e_t) * 1000.0) / 1000.0
@@ -462,8 +521,12 @@ def main():
            "h2d_bytes_per_step": 4 * n * n,
            "d2h_bytes_per_step": 32 * nbars, "ms_per_step": 1000 * e2e_s}
 
+    batched, kept = (None, None) if args.no_batched else measure_batched(args, full=False)
+
     if rank == 0:
         cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline(w)
+        if batched is not None and not args.no_cpu_baseline and world == 1:
+            batched["cpu_reference_grad_check"] = batched_cpu_check(kept)
         line = {"metric": "rips_barcode_simplices_per_s", "value": value, "unit": "simplices/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64 integer ranks and indices; f32 values",
@@ -472,7 +535,7 @@ def main():
                 "per_dim": per_dim, "barcode_ms": ms_per_step, "bars": nbars,
                 "kernel_ms": {k: v[0] for k, v in km.items()},
                 "roofline": roof, "roofline_streaming": streaming, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches, "clocks": ck}
+                "gpu_launches": launches, "clocks": ck, "batched": batched}
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -681,6 +681,54 @@ __device__ uint64_t pivot_apparent_facet(const DimArgs& a, const CV& cv, const B
   return fidx;
 }
 
+// Owner of the pivot row `key` of a column of cloud cl: the zero apparent facet
+// of the row (Section 4, "Persistence pairs": apparent pairs are not in the
+// table), else the table's owner (0xFFFFFFFF: none).  With the recorded pair
+// map the two lookups run at once on lanes 0 and 1.  Warp-cooperative; every
+// lane gets the results.
+__device__ __forceinline__ uint64_t pivot_owner(const DimArgs& a, const RedState& s, const CV& cv, const Binom& B,
+                                                int lane, uint32_t cl, uint64_t key, uint32_t* frank, uint32_t* tcoef,
+                                                uint32_t* owner) {
+  const uint64_t tkey = table_key(a, cl, row_key_idx(a, key));
+  if (a.amap) {
+    // lane 0 probes the pair map, lane 1 the pivot table, with the same load
+    // instructions, so the two lookups take the time of one
+    uint64_t val = 0;
+    int found = 0;
+    if (lane < 2) {
+      const uint64_t mask = lane == 0 ? a.amap_mask : s.t_mask;
+      uint64_t h = mix(tkey) & mask;
+      for (uint64_t probe = 0; probe <= mask; ++probe) {
+        const uint64_t* kp = lane == 0 ? a.amap + 2 * h : s.t_keys + h;
+        const uint64_t cur = *kp;
+        if (cur == tkey) {
+          found = 1;
+          break;
+        }
+        if (cur == IDX_NONE) break;
+        h = (h + 1) & mask;
+      }
+      if (found) val = lane == 0 ? a.amap[2 * h + 1] : (uint64_t)s.t_vals[h];
+    }
+    const int ffound = __shfl_sync(0xffffffffu, found, 0);
+    const uint64_t v = __shfl_sync(0xffffffffu, val, 0);
+    const int tfound = __shfl_sync(0xffffffffu, found, 1);
+    const uint64_t tv = __shfl_sync(0xffffffffu, val, 1);
+    *owner = tfound ? (uint32_t)tv : 0xFFFFFFFFu;
+    if (!ffound) return IDX_NONE;
+    *frank = row_key_rank(a, key);
+    *tcoef = ((a.d - (int)(v & 15)) & 1) ? a.p - 1 : 1u;
+    return v >> 4;
+  }
+  const uint64_t fidx = pivot_apparent_facet(a, cv, B, lane, cl, key, frank, tcoef);
+  *owner = 0xFFFFFFFFu;
+  if (fidx == IDX_NONE) {
+    const int64_t slot = table_find(s.t_keys, s.t_mask, tkey);
+    *owner = slot >= 0 ? s.t_vals[slot] : 0xFFFFFFFFu;
+  }
+  return fidx;
+}
+
 // ---------------------------------------------------------------- working columns
 // A column that has to be reduced keeps R_j = D V_j materialised in the R arena,
 // sorted by row key (oldest row first) with nonzero coefficients: the GPU form of
@@ -1034,7 +1082,6 @@ struct Chain {
   uint32_t coef;
   int64_t owner;  // table owner of the pivot, or -1 to look it up
   bool started;   // R_j's own run is in place
-  uint32_t pcoef; // block mode: pivot coefficient of the column being generated
   unsigned long long t0;  // globaltimer when the chain passed 255 additions
 };
 
@@ -1073,24 +1120,15 @@ __device__ __forceinline__ void chain_add(const DimArgs& a, const RedState& s, C
 // by that facet's column (Section 4, "Persistence pairs").  In warp mode a
 // chain longer than `limit` additions, or one needing a merge of more than
 // DimArgs::merge_max entries, stops with CH_HEAVY before anything is written back:
-// the column is then reduced block-wide from its last stored state.
-// In warp mode (block == false) the warp merges runs and generates coboundaries
-// itself.  In block mode these are handed back to the block: CH_MERGE with the
-// lanes of the runs, CH_GEN with the simplex whose coboundary is to be added
-// (its pivot coefficient in ch.pcoef; chain_add goes on once it is made), and
-// CH_GEN_SELF for R_j's own entries, which block mode sets up first (a column
-// on the reduce list always takes at least one addition).
+// the column is then reduced block-wide from its last stored state.  The warp
+// merges runs and generates coboundaries itself (block mode: chainb_advance).
 __device__ int chain_advance(const DimArgs& a, const RedState& s, const CV& cv, const Binom& B, int lane,
                              const SortTile& tile, uint32_t j, uint64_t jidx, uint32_t jrank, uint32_t cl,
-                             uint32_t limit, bool block, Chain& ch, ChainReq* req) {
+                             uint32_t limit, Chain& ch) {
   for (;;) {
     if (ch.nr == 32) runs_pack(ch.r, lane, &ch.nr);  // every lane taken: drop the used-up runs
     const unsigned mm = runs_merge_mask(ch.r, lane, ch.nr);
     if (mm) {
-      if (block) {
-        req->mask = mm;
-        return CH_MERGE;
-      }
       if (__reduce_add_sync(0xffffffffu, (mm >> lane) & 1u ? ch.r.len - ch.r.cur : 0u) > a.merge_max)
         return CH_HEAVY;
       if (!runs_merge_warp(s, ch.r, lane, a.p, mm)) return CH_ARENA;
@@ -1104,37 +1142,18 @@ __device__ int chain_advance(const DimArgs& a, const RedState& s, const CV& cv, 
       if (ch.t0 == 0) ch.t0 = now;
       else if (now - ch.t0 > s.chain_ns) return CH_LONG;
     }
-    if (block && !ch.started) {
-      const uint32_t jn = s.r_len[j];
-      if (!jn) {
-        req->gidx = jidx;
-        req->grank = jrank;
-        return CH_GEN_SELF;
-      }
-      if (lane == 0) ch.r = make_run(s.r_key + s.r_off[j], s.r_coef + s.r_off[j], jn, 1, a.p);
-      ch.nr = 1;
-      ch.started = true;
-    }
     // the column owning the current pivot: an apparent facet, or the table's owner
     const uint64_t* wk;
     const uint32_t* wc;
     uint32_t wn, wcoef;
     if (ch.owner < 0) {
-      uint32_t frank, tcoef;
-      const uint64_t fidx = pivot_apparent_facet(a, cv, B, lane, cl, ch.key, &frank, &tcoef);
+      uint32_t frank, tcoef, k;
+      const uint64_t fidx = pivot_owner(a, s, cv, B, lane, cl, ch.key, &frank, &tcoef, &k);
       if (fidx == IDX_NONE) {
-        const int64_t slot = table_find(s.t_keys, s.t_mask, table_key(a, cl, row_key_idx(a, ch.key)));
-        const uint32_t k = slot >= 0 ? s.t_vals[slot] : 0xFFFFFFFFu;
         if (k >= j) return CH_DONE;             // free, or owned by a later column: claim it next round
         if (ch.step >= limit) return CH_HEAVY;  // long chain: a block takes the column over
         ch.owner = k;
         continue;
-      }
-      if (block) {
-        req->gidx = fidx;
-        req->grank = frank;
-        ch.pcoef = tcoef;
-        return CH_GEN;
       }
       if (!gen_sorted(a, s, cv, B, lane, tile, fidx, frank, &wk, &wc, &wn)) return CH_ARENA;
       wcoef = tcoef;
@@ -1149,12 +1168,6 @@ __device__ int chain_advance(const DimArgs& a, const RedState& s, const CV& cv, 
         uint64_t kidx;
         uint32_t kr, kcl;
         column_simplex(a, s, k, &kidx, &kr, &kcl);
-        if (block) {
-          req->gidx = kidx;
-          req->grank = kr;
-          ch.pcoef = wcoef;
-          return CH_GEN;
-        }
         if (!gen_sorted(a, s, cv, B, lane, tile, kidx, kr, &wk, &wc, &wn)) return CH_ARENA;
       }
     }
@@ -1212,7 +1225,7 @@ __device__ void chain_finish(const RedState& s, const Chain& ch, int lane, uint3
 __device__ int chain_warp(const DimArgs& a, const RedState& s, const CV& cv, const Binom& B, int lane,
                           const SortTile& tile, uint32_t j, uint64_t jidx, uint32_t jrank, uint32_t cl, uint32_t limit,
                           Chain& ch) {
-  int st = chain_advance(a, s, cv, B, lane, tile, j, jidx, jrank, cl, limit, false, ch, nullptr);
+  int st = chain_advance(a, s, cv, B, lane, tile, j, jidx, jrank, cl, limit, ch);
   if (st != CH_DONE) return st;
   if (ch.step && ch.key != IDX_NONE) {
     const unsigned m = chain_store_mask(ch, lane);
@@ -1276,7 +1289,7 @@ __device__ void init_column(const DimArgs& a, const RedState& s, const Binom& B,
   }
   __syncwarp();
   // during the first phase the table is empty: only apparent facets can own a pivot
-  Chain ch{empty_run(), 0, 0, key, coef, -1, false, 0, 0};
+  Chain ch{empty_run(), 0, 0, key, coef, -1, false, 0};
   const int st = chain_warp(a, s, cv, B, lane, tile, j, idx, r, cl, ~0u, ch);
   if (st == CH_HEAVY) {  // the block will start over from the first pivot
     if (lane == 0) {
@@ -1332,7 +1345,7 @@ __device__ void reduce_one(const DimArgs& a, const RedState& s, const Binom& B, 
   uint32_t jr, cl;
   column_simplex(a, s, j, &jidx, &jr, &cl);
   const CV cv = cloud_view(a, cl);
-  Chain ch{empty_run(), 0, 0, s.piv_key[j], s.piv_coef[j], -1, false, 0, 0};
+  Chain ch{empty_run(), 0, 0, s.piv_key[j], s.piv_coef[j], -1, false, 0};
   ch.owner = reduce_owner(a, s, j, cl, ch.key);
   if (ch.owner < 0) {
     set_error(a.err, ERRF_INTERNAL);
@@ -1964,11 +1977,273 @@ __device__ bool block_merge_runs(const RedState& s, MergeSmem& ms, MergeReq& q, 
   return true;
 }
 
+// ---------------------------------------------------------------- block mode: ring runs
+// In block mode warp 0 runs the chain as in warp mode, but every run's next
+// RING_W entries sit in a ring in shared memory (slot = a ring of the block's
+// 32): a step of the pivot search reads its heads from shared memory, and a
+// run refills its ring with one coalesced warp-wide load every RING_W entries,
+// instead of waiting on a global load at every step.
+constexpr uint32_t RING_W = 32;  // entries per ring (one per lane for a refill)
+
+struct Rings {
+  uint64_t* k;  // 32 slots of RING_W keys
+  uint32_t* c;  // and stored coefficients
+};
+
+struct RingRun {
+  const uint64_t* key;
+  const uint32_t* coef;
+  uint32_t len, cur, scale;
+  uint64_t hk;    // head key, ~0 once the run is used up
+  uint32_t hc;    // head coefficient times scale, mod p
+  uint32_t wend;  // the ring holds entries [wend - RING_W, wend) of the run (entry i at i mod RING_W)
+  uint32_t slot;
+};
+
+__device__ __forceinline__ RingRun ring_empty() {
+  RingRun r;
+  r.key = nullptr;
+  r.coef = nullptr;
+  r.len = r.cur = r.wend = 0;
+  r.scale = 1;
+  r.hk = ~0ull;
+  r.hc = 0;
+  r.slot = 0;
+  return r;
+}
+
+// Warp-wide: lane L's run (its fields set, cursor at cur) loads entries
+// [cur, cur + RING_W) into its ring, from the shared-memory copy (sk, sc;
+// indexed like the run) when there is one, and takes its head.
+__device__ __forceinline__ void ring_load(const Rings& R, RingRun& r, int lane, int L, uint32_t p,
+                                          const uint64_t* sk = nullptr, const uint32_t* sc = nullptr) {
+  const uint64_t* kp = (const uint64_t*)__shfl_sync(0xffffffffu, (unsigned long long)r.key, L);
+  const uint32_t* cp = (const uint32_t*)__shfl_sync(0xffffffffu, (unsigned long long)r.coef, L);
+  const uint32_t base = __shfl_sync(0xffffffffu, r.cur, L);
+  const uint32_t len = __shfl_sync(0xffffffffu, r.len, L);
+  const uint32_t slot = __shfl_sync(0xffffffffu, r.slot, L);
+  const uint32_t i = base + lane;
+  if (i < len) {
+    const uint32_t at = slot * RING_W + (i & (RING_W - 1));
+    R.k[at] = sk ? sk[i] : kp[i];
+    R.c[at] = p == 2 ? 1u : (sc ? sc[i] : cp[i]);
+  }
+  __syncwarp();
+  if (lane == L) {
+    r.wend = min(base + RING_W, len);
+    const uint32_t at = r.slot * RING_W + (r.cur & (RING_W - 1));
+    r.hk = r.cur < r.len ? R.k[at] : ~0ull;
+    r.hc = r.cur < r.len ? scaled(R.c[at], r.scale, p) : 0u;
+  }
+}
+
+// Warp-wide: a new run over n entries (scale) at lane L, in a free slot.
+__device__ __forceinline__ void ring_new(const Rings& R, RingRun& r, int lane, int L, int nr, const uint64_t* k,
+                                         const uint32_t* c, uint32_t n, uint32_t scale, uint32_t p,
+                                         const uint64_t* sk = nullptr, const uint32_t* sc = nullptr) {
+  const unsigned used = __reduce_or_sync(0xffffffffu, lane < nr && lane != L ? 1u << r.slot : 0u);
+  if (lane == L) {
+    r.key = k;
+    r.coef = c;
+    r.len = n;
+    r.cur = 0;
+    r.scale = scale;
+    r.slot = __ffs(~used) - 1;
+  }
+  ring_load(R, r, lane, L, p, sk, sc);
+}
+
+// Pivot of the ring runs: the smallest head key with a nonzero combined
+// coefficient; heads at a key whose coefficients cancel move on.
+__device__ __forceinline__ uint64_t ring_pivot(const Rings& R, RingRun& r, int lane, uint32_t p, uint32_t* coef_out) {
+  for (;;) {
+    const uint64_t m = warp_min_u64(r.hk);
+    if (m == ~0ull) {
+      *coef_out = 0;
+      return IDX_NONE;
+    }
+    const bool at = r.hk == m;
+    const uint32_t c = warp_coef_sum(at, r.hc, p);
+    if (c) {
+      *coef_out = c;
+      return m;
+    }
+    if (at) ++r.cur;
+    unsigned need = __ballot_sync(0xffffffffu, at && r.cur < r.len && r.cur >= r.wend);
+    while (need) {
+      const int L = __ffs(need) - 1;
+      need &= need - 1;
+      ring_load(R, r, lane, L, p);
+    }
+    if (at) {
+      const uint32_t x = r.slot * RING_W + (r.cur & (RING_W - 1));
+      r.hk = r.cur < r.len ? R.k[x] : ~0ull;
+      r.hc = r.cur < r.len ? scaled(R.c[x], r.scale, p) : 0u;
+    }
+  }
+}
+
+// move the runs that are not used up to lanes 0 .. nr-1 (rings stay in their slots)
+__device__ __forceinline__ void ring_pack(RingRun& r, int lane, int* nr) {
+  const unsigned live = __ballot_sync(0xffffffffu, lane < *nr && r.hk != ~0ull);
+  const int cnt = __popc(live);
+  const int src = lane < cnt ? (int)__fns(live, 0, lane + 1) : lane;
+  RingRun t;
+  t.key = (const uint64_t*)__shfl_sync(0xffffffffu, (unsigned long long)r.key, src);
+  t.coef = (const uint32_t*)__shfl_sync(0xffffffffu, (unsigned long long)r.coef, src);
+  t.len = __shfl_sync(0xffffffffu, r.len, src);
+  t.cur = __shfl_sync(0xffffffffu, r.cur, src);
+  t.scale = __shfl_sync(0xffffffffu, r.scale, src);
+  t.hk = __shfl_sync(0xffffffffu, r.hk, src);
+  t.hc = __shfl_sync(0xffffffffu, r.hc, src);
+  t.wend = __shfl_sync(0xffffffffu, r.wend, src);
+  t.slot = __shfl_sync(0xffffffffu, r.slot, src);
+  r = lane < cnt ? t : ring_empty();
+  *nr = cnt;
+}
+
+// size class of a ring run's remaining entries (-1 when used up), as run_tier
+__device__ __forceinline__ int ring_tier(const RingRun& r) {
+  const uint32_t n = r.len - r.cur;
+  return r.hk != ~0ull && n ? (31 - __clz(n)) >> 1 : -1;
+}
+
+// runs_merge_mask for ring runs
+__device__ __forceinline__ unsigned ring_merge_mask(const RingRun& r, int lane, int nr) {
+  const int t = lane < nr ? ring_tier(r) : -1;
+  const unsigned grp = __match_any_sync(0xffffffffu, t >= 0 ? t : -2 - lane);
+  const unsigned elig =
+      __ballot_sync(0xffffffffu, t >= 0 && __popc(grp) >= (t < SHORT_TIERS ? MERGE_GROUP_SHORT : MERGE_GROUP));
+  if (elig) return __shfl_sync(0xffffffffu, grp, __ffs(elig) - 1);
+  if (nr == 32) {
+    const unsigned score = t >= 0 ? ((unsigned)__popc(grp) << 8) | (255u - (unsigned)t) : 0u;
+    const unsigned best = __reduce_max_sync(0xffffffffu, score);
+    return __shfl_sync(0xffffffffu, grp, __ffs(__ballot_sync(0xffffffffu, score == best)) - 1);
+  }
+  return 0;
+}
+
+// State of a heavy column's chain, held by warp 0 of the block that runs it.
+struct ChainB {
+  RingRun r;
+  int nr;
+  uint32_t step;
+  uint64_t key;
+  uint32_t coef;
+  int64_t owner;
+  bool started;
+  uint32_t pcoef;  // pivot coefficient of the column being generated
+  unsigned long long t0;
+};
+
+// R_j <- R_j - lambda C (Algorithm 1): C joins as a new run, then the new pivot
+__device__ __forceinline__ void chainb_add(const DimArgs& a, const RedState& s, const Rings& R, ChainB& ch, int lane,
+                                           const uint64_t* wk, const uint32_t* wc, uint32_t wn, uint32_t wcoef,
+                                           const uint64_t* sk = nullptr, const uint32_t* sc = nullptr) {
+  const uint32_t lam = (uint32_t)(((uint64_t)ch.coef * mod_inv(wcoef, a.p)) % a.p);
+  ring_new(R, ch.r, lane, ch.nr, ch.nr, wk, wc, wn, (a.p - lam) % a.p, a.p, sk, sc);
+  ++ch.nr;
+  ++ch.step;
+  if (lane == 0) {
+    atomicAdd(s.added, (unsigned long long)wn);
+    if ((ch.step & 15) == 0) atomicAdd(s.heartbeat, 1u);  // progress, for the grid barrier
+  }
+  ch.key = ring_pivot(R, ch.r, lane, a.p, &ch.coef);
+  ch.owner = -1;
+}
+
+// The block-mode chain (see chain_advance, whose block-mode branches it
+// follows): merges and generated coboundaries are handed to the block as
+// CH_MERGE, CH_GEN and CH_GEN_SELF requests.
+__device__ int chainb_advance(const DimArgs& a, const RedState& s, const CV& cv, const Binom& B, const Rings& R,
+                              int lane, uint32_t j, uint32_t cl, ChainB& ch, ChainReq* req, uint64_t jidx,
+                              uint32_t jrank) {
+  for (;;) {
+    if (ch.nr == 32) ring_pack(ch.r, lane, &ch.nr);  // every lane taken: drop the used-up runs
+    const unsigned mm = ring_merge_mask(ch.r, lane, ch.nr);
+    if (mm) {
+      req->mask = mm;
+      return CH_MERGE;
+    }
+    if (ch.key == IDX_NONE) return CH_DONE;
+    if (ch.step > MAX_PIVOT_PASSES) return CH_LONG;
+    if ((ch.step & 255) == 255) {  // the chain's wall-clock bound
+      const unsigned long long now = __shfl_sync(0xffffffffu, global_ns(), 0);
+      if (ch.t0 == 0) ch.t0 = now;
+      else if (now - ch.t0 > s.chain_ns) return CH_LONG;
+    }
+    if (!ch.started) {
+      const uint32_t jn = s.r_len[j];
+      if (!jn) {
+        req->gidx = jidx;
+        req->grank = jrank;
+        return CH_GEN_SELF;
+      }
+      ring_new(R, ch.r, lane, 0, 0, s.r_key + s.r_off[j], s.r_coef + s.r_off[j], jn, 1, a.p);
+      ch.nr = 1;
+      ch.started = true;
+    }
+    if (ch.owner < 0) {
+      uint32_t frank, tcoef, k;
+      const uint64_t fidx = pivot_owner(a, s, cv, B, lane, cl, ch.key, &frank, &tcoef, &k);
+      if (fidx == IDX_NONE) {
+        if (k >= j) return CH_DONE;  // free, or owned by a later column: claim it next round
+        ch.owner = k;
+        continue;
+      }
+      req->gidx = fidx;
+      req->grank = frank;
+      ch.pcoef = tcoef;
+      return CH_GEN;
+    }
+    const uint32_t k = (uint32_t)ch.owner;
+    const uint32_t wcoef = s.piv_coef[k];
+    const uint32_t kn = s.r_len[k];
+    if (!kn) {
+      uint64_t kidx;
+      uint32_t kr, kcl;
+      column_simplex(a, s, k, &kidx, &kr, &kcl);
+      req->gidx = kidx;
+      req->grank = kr;
+      ch.pcoef = wcoef;
+      return CH_GEN;
+    }
+    const unsigned long long ko = s.r_off[k];
+    chainb_add(a, s, R, ch, lane, s.r_key + ko, s.r_coef + ko, kn, wcoef);
+  }
+}
+
+__device__ __forceinline__ unsigned chainb_store_mask(const ChainB& ch, int lane) {
+  const unsigned live = __ballot_sync(0xffffffffu, lane < ch.nr && ch.r.hk != ~0ull);
+  const unsigned sc = __ballot_sync(0xffffffffu, lane < ch.nr && ch.r.hk != ~0ull && ch.r.scale != 1);
+  return (__popc(live) > 1 || sc) ? live : 0u;
+}
+
+__device__ void chainb_finish(const RedState& s, const ChainB& ch, int lane, uint32_t j, uint32_t* claim_count) {
+  const RingRun& r = ch.r;
+  const uint32_t src = __ffs(__ballot_sync(0xffffffffu, lane < ch.nr && r.hk != ~0ull)) - 1;
+  const unsigned long long off = __shfl_sync(0xffffffffu, (unsigned long long)(r.key + r.cur), src & 31);
+  const uint32_t len = __shfl_sync(0xffffffffu, r.len - r.cur, src & 31);
+  if (lane != 0) return;
+  if (ch.step) {
+    s.reduced[j] |= 1;
+    atomicAdd(s.steps, (unsigned long long)ch.step);
+    atomicMax(s.max_chain, ch.step);
+    if (ch.key != IDX_NONE) {
+      s.r_off[j] = (unsigned long long)((const uint64_t*)off - s.r_key);
+      s.r_len[j] = len;
+    }
+  }
+  s.piv_key[j] = ch.key;
+  s.piv_coef[j] = ch.coef;
+  if (ch.key != IDX_NONE) s.claim_list[atomicAdd(claim_count, 1u)] = j;
+}
+
 // Column j, reduced by the whole block (see block mode): warp 0 runs the chain,
 // and the block generates coboundaries and merges runs when warp 0 asks for it.
 // The chain has no step limit here.  A heavy column given up by a warp may come
 // with a pivot nobody owns yet; the chain then ends at once and claims it.
-__device__ void reduce_one_block(const DimArgs& a, const RedState& s, const Binom& B, const SortTile& tile,
+__device__ void reduce_one_block(const DimArgs& a, const RedState& s, const Binom& B, const Rings& R,
                                  unsigned char* raw, MergeReq& q, uint32_t j, uint32_t* claim_count) {
   const uint32_t tid = threadIdx.x;
   const int lane = tid & 31;
@@ -1976,7 +2251,7 @@ __device__ void reduce_one_block(const DimArgs& a, const RedState& s, const Bino
   uint32_t jr, cl;
   column_simplex(a, s, j, &jidx, &jr, &cl);
   const CV cv = cloud_view(a, cl);
-  Chain ch{empty_run(), 0, 0, 0, 0, -1, false, 0, 0};  // meaningful in warp 0 only
+  ChainB ch{ring_empty(), 0, 0, 0, 0, -1, false, 0, 0};  // meaningful in warp 0 only
   bool finishing = false;
   if (tid < 32) {
     ch.key = s.piv_key[j];
@@ -1988,11 +2263,11 @@ __device__ void reduce_one_block(const DimArgs& a, const RedState& s, const Bino
     if (tid < 32) {
       ChainReq cr{0u, 0ull, 0u};
       int st = CH_DONE;
-      if (!finishing) st = chain_advance(a, s, cv, B, lane, tile, j, jidx, jr, cl, ~0u, true, ch, &cr);
+      if (!finishing) st = chainb_advance(a, s, cv, B, R, lane, j, cl, ch, &cr, jidx, jr);
       if (st == CH_DONE && !finishing) {  // the chain ended: R_j must become one run
         finishing = true;
         if (ch.step && ch.key != IDX_NONE) {
-          cr.mask = chain_store_mask(ch, lane);
+          cr.mask = chainb_store_mask(ch, lane);
           if (cr.mask) st = CH_MERGE;
         }
       }
@@ -2019,11 +2294,20 @@ __device__ void reduce_one_block(const DimArgs& a, const RedState& s, const Bino
         state = CH_ARENA;
         break;
       }
-      if (tid < 32) {  // the merged run replaces the runs it was made of
+      if (tid < 32) {  // the merged run replaces the runs it was made of, in the lowest one's slot
         const unsigned mask = q.mask;
-        if (lane == __ffs(mask) - 1) ch.r = make_run(q.d[0].key, q.d[0].coef, q.d[0].len, 1, a.p);
-        else if ((mask >> lane) & 1u) ch.r = empty_run();
-        runs_pack(ch.r, lane, &ch.nr);
+        const int L = __ffs(mask) - 1;
+        if (lane == L) {
+          ch.r.key = q.d[0].key;
+          ch.r.coef = q.d[0].coef;
+          ch.r.len = q.d[0].len;
+          ch.r.cur = 0;
+          ch.r.scale = 1;
+        } else if ((mask >> lane) & 1u) {
+          ch.r = ring_empty();
+        }
+        ring_load(R, ch.r, lane, L, a.p);
+        ring_pack(ch.r, lane, &ch.nr);
       }
     } else if (state == CH_GEN || state == CH_GEN_SELF) {
       RunDesc g;
@@ -2035,11 +2319,11 @@ __device__ void reduce_one_block(const DimArgs& a, const RedState& s, const Bino
       }
       if (tid < 32) {
         if (state == CH_GEN_SELF) {
-          if (lane == 0) ch.r = make_run(g.key, g.coef, g.len, 1, a.p, gk, gc);
+          ring_new(R, ch.r, lane, 0, 0, g.key, g.coef, g.len, 1, a.p, gk, gc);
           ch.nr = 1;
           ch.started = true;
         } else {
-          chain_add(a, s, ch, lane, g.key, g.coef, g.len, ch.pcoef, gk, gc);
+          chainb_add(a, s, R, ch, lane, g.key, g.coef, g.len, ch.pcoef, gk, gc);
         }
       }
     } else {
@@ -2051,7 +2335,7 @@ __device__ void reduce_one_block(const DimArgs& a, const RedState& s, const Bino
     if (lane == 0) chain_error(a, state);
     return;
   }
-  chain_finish(s, ch, lane, j, claim_count);
+  chainb_finish(s, ch, lane, j, claim_count);
 }
 
 
@@ -2120,6 +2404,10 @@ __global__ void __launch_bounds__(256, 2) reduce_persistent_kernel(DimArgs a, Re
   // the warps' sort tiles, or one merge tile for the whole block in block mode
   __shared__ __align__(16) unsigned char red_smem[RED_SMEM_BYTES];
   __shared__ MergeReq req;
+  // rings of the block-mode chain's runs
+  __shared__ uint64_t ring_k[32 * RING_W];
+  __shared__ uint32_t ring_c[32 * RING_W];
+  const Rings rings{ring_k, ring_c};
   if (threadIdx.x == 0) req.chunk_left = 0;  // visible to the block after the first grid barrier
   const uint32_t w = threadIdx.x >> 5;
   const SortTile tile{(uint64_t*)red_smem + w * SORT_TILE,
@@ -2161,9 +2449,9 @@ __global__ void __launch_bounds__(256, 2) reduce_persistent_kernel(DimArgs a, Re
     const uint32_t nheavy = *(volatile unsigned*)&heavy_cnt[src];
     if (nred + nheavy <= gridDim.x) {  // few columns left: one block per column
       const uint32_t t = blockIdx.x;
-      if (t < nheavy) reduce_one_block(a, s, B, tile, red_smem, req, heavy[src][t], &claim_cnt[dst]);
+      if (t < nheavy) reduce_one_block(a, s, B, rings, red_smem, req, heavy[src][t], &claim_cnt[dst]);
       else if (t < nheavy + nred)
-        reduce_one_block(a, s, B, tile, red_smem, req, s.reduce_list[t - nheavy], &claim_cnt[dst]);
+        reduce_one_block(a, s, B, rings, red_smem, req, s.reduce_list[t - nheavy], &claim_cnt[dst]);
     } else {
       for (;;) {  // heavy columns: a block each
         if (threadIdx.x == 0) req.take = atomicAdd(heavy_next, 1u);
@@ -2171,7 +2459,7 @@ __global__ void __launch_bounds__(256, 2) reduce_persistent_kernel(DimArgs a, Re
         const uint32_t t = req.take;
         __syncthreads();
         if (t >= nheavy) break;
-        reduce_one_block(a, s, B, tile, red_smem, req, heavy[src][t], &claim_cnt[dst]);
+        reduce_one_block(a, s, B, rings, red_smem, req, heavy[src][t], &claim_cnt[dst]);
       }
       for (;;) {  // the others: a warp each
         uint32_t t = 0;
@@ -2213,6 +2501,10 @@ __global__ void readout_kernel(DimArgs a, RedState s, const float* __restrict__ 
       const uint32_t tr = row_key_rank(a, key);
       if (tr == r) {
         atomicAdd(&st[1], 1ull);
+        continue;
+      }
+      if (tr > a.rank_max) {  // not a row of this filtration: a broken reduction, not a bar
+        set_error(a.err, ERRF_INTERNAL);
         continue;
       }
       b.death = rank_value[tr];

@@ -81,3 +81,60 @@ def test_batch_matches_golden():
         h0 = [(d, b, e, bs, -1 if ds == U64MAX else ds) for d, b, e, bs, ds in _key_gpu(res.dim(0, c))]
         assert len(h0) == head["h0_count"], c
         assert mg.canonical_digest(h0) == head["h0_digest"], c
+
+
+def _gold_batch():
+    path = os.path.join(GOLD, "batch256.bars.txt.gz")
+    if not os.path.exists(path):
+        pytest.skip("golden file batch256 not generated")
+    return _mg().read_batch(path)
+
+
+def test_batch_plan_graph_replay_matches_golden():
+    """The CUDA-graph replay of a batch plan over all 256 clouds against the
+    oracle's stored barcodes (H1 bar by bar, H0 by count and digest)."""
+    import torch
+    import paper_1908_02518_gb300 as rg
+    clouds = W.batch_clouds()
+    off = np.concatenate([[0], np.cumsum([c.shape[0] for c in clouds])]).astype(np.int64)
+    gold = _gold_batch()
+    mg = _mg()
+    x = torch.from_numpy(np.concatenate(clouds)).cuda()
+    plan = rg.BatchPlan(off, 3)
+    graph = plan.capture(x)
+    graph.replay()
+    res = plan.result()
+    for c in range(len(clouds)):
+        head, h1 = gold[c]
+        assert _key_gpu(res.dim(1, c)) == _key_gold(h1), c
+        h0 = [(d, b, e, bs, -1 if ds == U64MAX else ds) for d, b, e, bs, ds in _key_gpu(res.dim(0, c))]
+        assert len(h0) == head["h0_count"], c
+        assert mg.canonical_digest(h0) == head["h0_digest"], c
+    plan.free()
+
+
+def test_batch_gradient_matches_cpu_reference():
+    """Forward + backward of loss = sum over H1 bars of (death - birth)^2 on all
+    256 clouds in one batched call; every cloud's gradient against the CPU
+    reference gradient (oracle/gradients.py) on the oracle's stored pairs,
+    ||g - g_ref||_inf <= 1e-4 max(||g_ref||_inf, 1e-6)."""
+    import torch
+    import paper_1908_02518_gb300 as rg
+    from oracle import gradients as G
+    clouds = W.batch_clouds()
+    off = np.concatenate([[0], np.cumsum([c.shape[0] for c in clouds])]).astype(np.int64)
+    gold = _gold_batch()
+    x = torch.from_numpy(np.concatenate(clouds)).cuda().requires_grad_(True)
+    birth, death, dim, cloud = rg.RipsBarcodes.apply(x, off.tolist(), 1)
+    fin = torch.isfinite(death) & (dim == 1)
+    ((death - birth)[fin] ** 2).sum().backward()
+    g = x.grad.double().cpu().numpy()
+    dt = np.dtype([("dim", "i4"), ("birth", "f4"), ("death", "f4"), ("birth_simplex", "i8"), ("death_simplex", "i8")])
+    for c, pts in enumerate(clouds):
+        _, h1 = gold[c]
+        bars = np.array([(d, b, e, bs, ds) for d, b, e, bs, ds in h1 if ds >= 0], dtype=dt)
+        diff = bars["death"].astype(np.float64) - bars["birth"].astype(np.float64)
+        ref = G.bar_gradient(pts, bars, -2 * diff, 2 * diff)
+        gc = g[off[c]:off[c + 1]]
+        err = np.abs(gc - ref).max() if len(ref) else 0.0
+        assert err <= 1e-4 * max(np.abs(ref).max() if len(ref) else 0.0, 1e-6), (c, err)
