@@ -114,6 +114,21 @@ RIPS_API int rips_barcodes_device(const float* d_dist, int64_t n, int32_t dim_ma
                                   uint32_t p, void* cuda_stream, rips_result_t** out);
 
 /*
+ * rips_barcodes_packed -- the same problem for a distance matrix given as its
+ * strict lower or upper triangle, packed row by row (the triangular input
+ * formats of Section 4, "Input"): layout RIPS_LOWER_TRIANGLE holds d(1,0),
+ * d(2,0), d(2,1), d(3,0), ...; RIPS_UPPER_TRIANGLE holds d(0,1), d(0,2), ...,
+ * d(0,n-1), d(1,2), ....  d_packed: n(n-1)/2 FP32 entries in DEVICE memory
+ * (read only, owned by the caller; may be NULL when n = 1); the matrix is
+ * expanded into library-owned device memory on cuda_stream.  Entry rules,
+ * threshold, p, statuses and the result as for rips_barcodes; an unknown
+ * layout is RIPS_ERR_BAD_ARG.
+ */
+enum rips_layout { RIPS_LOWER_TRIANGLE = 0, RIPS_UPPER_TRIANGLE = 1 };
+RIPS_API int rips_barcodes_packed(const float* d_packed, int64_t n, int32_t layout, int32_t dim_max,
+                                  float threshold, uint32_t p, void* cuda_stream, rips_result_t** out);
+
+/*
  * rips_distance_matrix_device -- the finite metric space of a point cloud
  * (Section 4 "Input" accepts point clouds as well as distance matrices):
  * Euclidean distances of n points with k FP32

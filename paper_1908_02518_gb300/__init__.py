@@ -20,7 +20,7 @@ import numpy as np
 from . import _lib
 from ._lib import RipsError
 
-__all__ = ["barcodes", "barcodes_batched", "barcodes_batched_dists", "distance_matrix", "backward",
+__all__ = ["barcodes", "barcodes_packed", "barcodes_batched", "barcodes_batched_dists", "distance_matrix", "backward",
            "backward_dist", "Result", "RipsError",
            "RipsBarcodes", "launch_count", "set_kernel_timing", "BAR_DTYPE"]
 
@@ -130,6 +130,25 @@ def barcodes(dist, dim_max: int = 1, threshold: float = math.inf, p: int = 2, st
         st = lib.rips_barcodes(d.ctypes.data_as(C.POINTER(C.c_float)), d.shape[0], dim_max, C.c_float(threshold),
                                p, C.byref(out))
     _lib.check(st, "rips_barcodes")
+    return _collect(lib, out, keep_handle)
+
+
+def barcodes_packed(packed, n: int, layout: str = "lower", dim_max: int = 1, threshold: float = math.inf,
+                    p: int = 2, stream=None, keep_handle: bool = False) -> Result:
+    """Barcodes of a distance matrix given as its strict lower or upper
+    triangle packed row by row (n(n-1)/2 FP32 entries, a CUDA tensor or a host
+    array, which is copied to the device)."""
+    import torch
+    lib = _lib.load()
+    t = packed if hasattr(packed, "is_cuda") else torch.from_numpy(np.ascontiguousarray(packed, dtype=np.float32))
+    t = t.contiguous().float().cuda()
+    if t.numel() != n * (n - 1) // 2:
+        raise ValueError("packed triangle must hold n(n-1)/2 entries")
+    code = {"lower": 0, "upper": 1}[layout]
+    out = C.c_void_p()
+    st = lib.rips_barcodes_packed(C.c_void_p(t.data_ptr() if t.numel() else 0), n, code, dim_max,
+                                  C.c_float(threshold), p, _stream_ptr(stream), C.byref(out))
+    _lib.check(st, "rips_barcodes_packed")
     return _collect(lib, out, keep_handle)
 
 

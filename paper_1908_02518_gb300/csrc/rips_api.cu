@@ -1335,6 +1335,27 @@ RIPS_API int rips_barcodes(const float* dist, int64_t n, int32_t dim_max, float 
   }
 }
 
+RIPS_API int rips_barcodes_packed(const float* d_packed, int64_t n, int32_t layout, int32_t dim_max,
+                                  float threshold, uint32_t p, void* cuda_stream, rips_result_t** out) {
+  if (!out) return RIPS_ERR_BAD_ARG;
+  *out = nullptr;
+  if ((!d_packed && n > 1) || (layout != RIPS_LOWER_TRIANGLE && layout != RIPS_UPPER_TRIANGLE))
+    return RIPS_ERR_BAD_ARG;
+  int rc = check_args(n, dim_max, threshold, p);
+  if (rc != RIPS_OK) return rc;
+  try {
+    Workspace* w = current_workspace();
+    if (!w) return RIPS_ERR_OOM;
+    std::lock_guard<std::mutex> g(w->mu);
+    const cudaStream_t s = (cudaStream_t)cuda_stream;
+    CR(ensure(w->dist, (size_t)n * n * 4));
+    CK(launch_unpack_triangle(d_packed, (int)n, layout == RIPS_UPPER_TRIANGLE, P<float>(w->dist), s));
+    return barcodes_locked(*w, P<float>(w->dist), n, dim_max, threshold, p, s, out);
+  } catch (...) {
+    return RIPS_ERR_INTERNAL;
+  }
+}
+
 RIPS_API int rips_distance_matrix_device(const float* d_points, int64_t n, int32_t k, float* d_dist,
                                          void* cuda_stream) {
   if (!d_points || !d_dist || n < 1 || n > 46340 || k < 1) return RIPS_ERR_BAD_ARG;

@@ -135,6 +135,8 @@ cudaError_t launch_neighbor_counts(const uint32_t* R, const CloudInfo* clouds, c
 cudaError_t launch_neighbor_fill(const uint32_t* R, const CloudInfo* clouds, const uint32_t* vcloud, uint32_t nverts,
                                  const uint32_t* off, uint32_t* nbr, cudaStream_t s);
 cudaError_t launch_distance_matrix(const float* pts, int n, int k, float* D, cudaStream_t s);
+// packed strict triangle (lower: row by row from row 1; upper: row by row to row n-2) -> strict lower triangle of D
+cudaError_t launch_unpack_triangle(const float* packed, int n, int upper, float* D, cudaStream_t s);
 cudaError_t launch_pad_past_count(uint64_t* keys, const uint32_t* count, uint64_t cap, cudaStream_t s);
 cudaError_t launch_cloud_edge_offsets(CloudInfo* clouds, const uint32_t* ccounts, int nclouds, cudaStream_t s);
 cudaError_t launch_distance_matrices(const float* pts, int k, const CloudInfo* clouds, const uint32_t* tile_off,

@@ -400,6 +400,28 @@ cudaError_t launch_distance_matrix(const float* pts, int n, int k, float* D, cud
 }
 
 
+// Strict triangle of a distance matrix stored packed (row by row) into the
+// strict lower triangle of the n x n matrix D: lower layout, entry (i, j) with
+// i > j at i(i-1)/2 + j (rows 1 .. n-1 of the lower triangle, each from column
+// 0); upper layout, entry (r, c) with r < c at r n - r(r+1)/2 + (c - r - 1)
+// (rows 0 .. n-2 of the upper triangle).  Only D[i][j], i > j, is written.
+__global__ void unpack_triangle_kernel(const float* __restrict__ packed, int n, int upper, float* __restrict__ D) {
+  const int i = blockIdx.y * blockDim.y + threadIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || j >= i) return;
+  const uint64_t at = upper ? (uint64_t)j * n - (uint64_t)j * (j + 1) / 2 + (uint64_t)(i - j - 1)
+                            : (uint64_t)i * (i - 1) / 2 + (uint64_t)j;
+  D[(size_t)i * n + j] = packed[at];
+}
+
+cudaError_t launch_unpack_triangle(const float* packed, int n, int upper, float* D, cudaStream_t s) {
+  if (n < 2) return cudaSuccess;
+  dim3 blk(32, 8), grd((n + 31) / 32, (n + 7) / 8);
+  unpack_triangle_kernel<<<grd, blk, 0, s>>>(packed, n, upper, D);
+  note_launch();
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- batch plans (no host reads)
 // Entries [*count, cap) of a key list set to the largest key, so a sort of all
 // cap entries leaves the real ones first.

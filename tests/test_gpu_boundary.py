@@ -93,3 +93,19 @@ def test_backward_dist_equals_points_backward_grad_dist():
     rg.backward(res, x, gb, gd, grad_dist=g2)
     np.testing.assert_allclose(g1.cpu().numpy().ravel(), g2.cpu().numpy(), rtol=1e-6, atol=1e-6)
     res.free()
+
+
+@pytest.mark.parametrize("layout", ["lower", "upper"])
+def test_packed_triangle_matches_oracle(oracle_mod, layout):
+    """The packed lower / upper triangle input formats give the oracle's bars of
+    the full matrix, bar by bar."""
+    import paper_1908_02518_gb300 as rg
+    for d, t, p in [(W.distance_matrix(W.torus_points(120, 61)), 1.2, 2), (W.random_integer_matrix(25, 62), math.inf, 3)]:
+        n = d.shape[0]
+        if layout == "lower":
+            packed = np.concatenate([d[i, :i] for i in range(1, n)])
+        else:
+            packed = np.concatenate([d[i, i + 1:] for i in range(n - 1)])
+        got = rg.barcodes_packed(packed.astype(np.float32), n, layout, 2, t, p)
+        want = oracle_mod.barcodes(d, 2, t, p)
+        assert _key(got.bars) == _key(want.bars)
