@@ -336,6 +336,21 @@ typedef struct rips_limits {
 RIPS_API int rips_set_limits(const rips_limits_t* limits);
 RIPS_API int rips_get_limits(rips_limits_t* out);
 
+/* Ablation switches (the experiment of Table 3 of the paper): with
+ * RIPS_OPT_NO_APPARENT the zero-persistence apparent pairs of Section 3.5 are
+ * not skipped -- every simplex that is not cleared becomes a column and every
+ * pivot is owned through the pivot table; with RIPS_OPT_NO_EMERGENT the first
+ * pivot of a column is found by scanning its whole coboundary instead of
+ * stopping at the first cofacet of the column's own diameter (the emergent-pair
+ * shortcut of Section 3.5).  Neither switch changes any bar; the statistics of
+ * Table 2 (rips_result_stats) show what each shortcut saved.  The library keeps
+ * the coboundary implicit and the reduced columns R_j in every setting (it does
+ * not store V, so R cannot be discarded).  Process-wide, later calls only;
+ * batch plans ignore the switches.  RIPS_ERR_BAD_ARG on an unknown bit. */
+enum rips_option { RIPS_OPT_NO_APPARENT = 1, RIPS_OPT_NO_EMERGENT = 2 };
+RIPS_API int rips_set_options(uint32_t flags);
+RIPS_API uint32_t rips_get_options(void);
+
 /* Batch plans (the batched problem of rips_barcodes_batched for barcodes H0 and
  * H1, with every launch fixed in advance).  A plan is made once for a list of
  * cloud sizes (`offsets`, batch + 1 point offsets as in rips_barcodes_batched),

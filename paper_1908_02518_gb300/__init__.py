@@ -250,6 +250,18 @@ def set_limits(barrier_wait_ns: int = 0, chain_ns: int = 0, arena_entries: int =
     _lib.check(_lib.load().rips_set_limits(C.byref(lim)), "rips_set_limits")
 
 
+def set_options(apparent: bool = True, emergent: bool = True) -> None:
+    """Ablation switches (Table 3 of the paper): turn the apparent-pair skip or
+    the emergent first-pivot shortcut off for later calls; bars never change."""
+    flags = (0 if apparent else 1) | (0 if emergent else 2)
+    _lib.check(_lib.load().rips_set_options(flags), "rips_set_options")
+
+
+def get_options() -> dict:
+    f = int(_lib.load().rips_get_options())
+    return {"apparent": not (f & 1), "emergent": not (f & 2)}
+
+
 def get_limits() -> dict:
     lim = _lib.Limits()
     _lib.check(_lib.load().rips_get_limits(C.byref(lim)), "rips_get_limits")

@@ -46,7 +46,7 @@ EXPORTS = [
     "rips_result_dim_max", "rips_result_threshold", "rips_result_stats", "rips_result_phase_ms",
     "rips_result_free", "rips_status_string", "rips_kernel_launch_count", "rips_set_kernel_timing",
     "rips_result_kernel_ms", "rips_h0_barcode_noalloc", "rips_set_tuning", "rips_get_tuning", "rips_clear_tuning",
-    "rips_set_limits", "rips_get_limits", "rips_batch_plan_create", "rips_batch_plan_run", "rips_batch_plan_result",
+    "rips_set_limits", "rips_get_limits", "rips_set_options", "rips_get_options", "rips_batch_plan_create", "rips_batch_plan_run", "rips_batch_plan_result",
     "rips_batch_plan_free",
 ]
 
@@ -121,6 +121,10 @@ def load(build_if_missing: bool = True):
     lib.rips_clear_tuning.restype = None
     lib.rips_set_limits.argtypes = [C.POINTER(Limits)]
     lib.rips_set_limits.restype = C.c_int
+    lib.rips_set_options.argtypes = [u32]
+    lib.rips_set_options.restype = C.c_int
+    lib.rips_get_options.argtypes = []
+    lib.rips_get_options.restype = u32
     lib.rips_get_limits.argtypes = [C.POINTER(Limits)]
     lib.rips_get_limits.restype = C.c_int
     lib.rips_batch_plan_create.argtypes = [C.POINTER(C.c_int64), i32, i32, C.c_float, u32, i64, pres]

@@ -201,6 +201,12 @@ constexpr rips_tuning_t TUNE_DEFAULT{32, 2048, 0, 16};
 
 std::mutex g_limits_mu;
 rips_limits_t g_limits{0, 0, 0, 0};
+uint32_t g_options = 0;  // RIPS_OPT_* (guarded by g_limits_mu)
+
+uint32_t current_options() {
+  std::lock_guard<std::mutex> g(g_limits_mu);
+  return g_options;
+}
 
 rips_limits_t current_limits() {
   std::lock_guard<std::mutex> g(g_limits_mu);
@@ -490,6 +496,7 @@ int run_batch(Workspace& w, const float* dD, const std::vector<int64_t>& ns, int
       a.reduce_blocks_per_sm = tu.reduce_blocks_per_sm;
       a.scan_blocks_per_sm = tu.scan_blocks_per_sm;
     }
+    a.opts = current_options();
     if (rank_bits + a.row_bits > 63 || cb + rank_bits + a.col_bits > 64 || cb + a.row_bits > 64)
       return RIPS_ERR_OVERFLOW;
     unsigned long long* st = dstats + d * 16;  // cloud c: st + c * SPC
@@ -536,7 +543,8 @@ int run_batch(Workspace& w, const float* dD, const std::vector<int64_t>& ns, int
     // map of this dimension's zero apparent pairs (at most one per tested simplex)
     uint64_t acap = 16;
     while (acap < 2ull * nsd + 16) acap <<= 1;
-    if (a.col_bits <= 60 && acap * 16 <= (16ull << 30)) {  // else the test and reduction scan instead
+    if (!(a.opts & RIPS_OPT_NO_APPARENT) && a.col_bits <= 60 &&
+        acap * 16 <= (16ull << 30)) {  // else the test and reduction scan instead
       CR(ensure(w.amk[cur], (size_t)acap * 16));
       CK(cudaMemsetAsync(w.amk[cur].p, 0xFF, (size_t)acap * 16, s));
       a.amap = P<uint64_t>(w.amk[cur]);
@@ -1047,6 +1055,7 @@ int plan_create(PlanState& pl, const int64_t* offsets, int32_t batch, int32_t k,
   }
   a.pmap = nullptr;
   a.pmap_mask = 0;
+  a.opts = 0;  // batch plans always take both shortcuts
   pl.tcap = pow2_at_least(2ull * pl.e_cap + 16);
   pl.acap = pow2_at_least(2ull * pl.e_cap + 16);
   if (arena_entries) {
@@ -1469,6 +1478,15 @@ RIPS_API int rips_set_limits(const rips_limits_t* limits) {
   g_limits = *limits;
   return RIPS_OK;
 }
+
+RIPS_API int rips_set_options(uint32_t flags) {
+  if (flags & ~(uint32_t)(RIPS_OPT_NO_APPARENT | RIPS_OPT_NO_EMERGENT)) return RIPS_ERR_BAD_ARG;
+  std::lock_guard<std::mutex> g(g_limits_mu);
+  g_options = flags;
+  return RIPS_OK;
+}
+
+RIPS_API uint32_t rips_get_options(void) { return current_options(); }
 
 RIPS_API int rips_get_limits(rips_limits_t* out) {
   if (!out) return RIPS_ERR_BAD_ARG;

@@ -509,10 +509,12 @@ __global__ void __launch_bounds__(256) test_kernel(DimArgs a, const uint64_t* __
     const CV cv = cloud_view(a, cl);
     int v[MAX_DIM + 2];
     decode(B, cv.n, idx, d, v);
-    // cofacet side: (sigma, tau) zero apparent pair?
+    // cofacet side: (sigma, tau) zero apparent pair?  (not with the apparent-pair
+    // shortcut switched off: every simplex that is not cleared is then a column)
+    const bool apparent = !(a.opts & RIPS_OPT_NO_APPARENT);
     uint32_t rj[MAX_DIM + 2];
-    int hl;
-    int j = first_equal_cofacet(cv, v, d, r, lane, rj, &hl);
+    int hl = -1;
+    int j = apparent ? first_equal_cofacet(cv, v, d, r, lane, rj, &hl) : -1;
     if (j >= 0) {
       int app = 0;
       if (lane == hl) {
@@ -548,7 +550,7 @@ __global__ void __launch_bounds__(256) test_kernel(DimArgs a, const uint64_t* __
     }
     // facet side (d >= 2; in dimension 1 such edges are spanning-forest edges):
     // the previous dimension's test recorded every zero apparent pair
-    if (d >= 2) {
+    if (apparent && d >= 2) {
       bool fac;
       if (a.pmap) {
         uint64_t unused;
@@ -690,6 +692,11 @@ __device__ __forceinline__ uint64_t pivot_owner(const DimArgs& a, const RedState
                                                 int lane, uint32_t cl, uint64_t key, uint32_t* frank, uint32_t* tcoef,
                                                 uint32_t* owner) {
   const uint64_t tkey = table_key(a, cl, row_key_idx(a, key));
+  if (a.opts & RIPS_OPT_NO_APPARENT) {  // apparent pairs are ordinary columns: the table owns every pivot
+    const int64_t slot = table_find(s.t_keys, s.t_mask, tkey);
+    *owner = slot >= 0 ? s.t_vals[slot] : 0xFFFFFFFFu;
+    return IDX_NONE;
+  }
   if (a.amap) {
     // lane 0 probes the pair map, lane 1 the pivot table, with the same load
     // instructions, so the two lookups take the time of one
@@ -1269,7 +1276,9 @@ __device__ void init_column(const DimArgs& a, const RedState& s, const Binom& B,
   decode(B, cv.n, idx, d, v);
   uint32_t rj[MAX_DIM + 2];
   int hl;
-  const int jv = first_equal_cofacet(cv, v, d, r, lane, rj, &hl);
+  // the first cofacet with the column's own diameter is its pivot; with the
+  // emergent shortcut switched off the whole coboundary is scanned instead
+  const int jv = (a.opts & RIPS_OPT_NO_EMERGENT) ? -1 : first_equal_cofacet(cv, v, d, r, lane, rj, &hl);
   uint64_t key;
   uint32_t coef;
   if (jv >= 0) {

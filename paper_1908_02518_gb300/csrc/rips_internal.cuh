@@ -188,6 +188,7 @@ struct DimArgs {
   uint32_t merge_max;              // largest run merge one warp makes
   int reduce_blocks_per_sm;        // 0: occupancy limit
   int scan_blocks_per_sm;
+  uint32_t opts;                   // RIPS_OPT_* switches (rips_set_options)
 };
 
 // Reduction state (device pointers) shared by the reduction kernels

@@ -63,3 +63,11 @@ def test_no_oracle_import_in_product():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "rips_oracle" not in txt, f
+
+
+def test_options_reject_unknown_bits():
+    from paper_1908_02518_gb300 import _lib
+    lib = _lib.load()
+    assert lib.rips_set_options(1 << 7) == -1
+    assert lib.rips_set_options(3) == 0 and lib.rips_get_options() == 3
+    assert lib.rips_set_options(0) == 0 and lib.rips_get_options() == 0
