@@ -836,8 +836,9 @@ struct Run {
   uint32_t nc[RUN_AHEAD];  // and their stored coefficients (not loaded over Z/2)
 };
 
+// c * scale mod p; both below p < 2^16, so the product fits in 32 bits
 __device__ __forceinline__ uint32_t scaled(uint32_t c, uint32_t scale, uint32_t p) {
-  return p == 2 ? 1u : (uint32_t)(((uint64_t)c * scale) % p);
+  return p == 2 ? 1u : (c * scale) % p;
 }
 
 // head and look-ahead from the cursor on
@@ -986,20 +987,24 @@ __device__ bool gen_sorted(const DimArgs& a, const RedState& s, const CV& cv, co
 
 // Pivot of the run set: the smallest head key with a nonzero combined
 // coefficient.  Heads at a key whose coefficients cancel are advanced.
-__device__ uint64_t runs_pivot(Run& r, uint32_t p, uint32_t* coef_out) {
+template <bool Z2>
+__device__ __forceinline__ uint64_t runs_pivot(Run& rs, uint32_t p, uint32_t* coef_out) {
+  Run r = rs;  // the search works on registers; the chain's copy may live in local memory
   for (;;) {
     const uint64_t m = warp_min_u64(r.hk);
     if (m == ~0ull) {
+      rs = r;
       *coef_out = 0;
       return IDX_NONE;
     }
     const bool at = r.hk == m;
-    const uint32_t c = warp_coef_sum(at, r.hc, p);
+    const uint32_t c = warp_coef_sum(at, r.hc, Z2 ? 2u : p);
     if (c) {
+      rs = r;
       *coef_out = c;
       return m;
     }
-    advance_if(r, at, p);
+    advance_if(r, at, Z2 ? 2u : p);
   }
 }
 
@@ -1115,7 +1120,7 @@ __device__ __forceinline__ void chain_add(const DimArgs& a, const RedState& s, C
     atomicAdd(s.added, (unsigned long long)wn);
     if ((ch.step & 15) == 0) atomicAdd(s.heartbeat, 1u);  // progress, for the grid barrier
   }
-  ch.key = runs_pivot(ch.r, a.p, &ch.coef);
+  ch.key = a.p == 2 ? runs_pivot<true>(ch.r, a.p, &ch.coef) : runs_pivot<false>(ch.r, a.p, &ch.coef);
   ch.owner = -1;
 }
 
@@ -1586,9 +1591,9 @@ __device__ uint32_t block_axpy(MergeSmem& ms, const RunDesc& A, const RunDesc& B
     for (uint32_t i = tid; i <= MERGE_T; i += blockDim.x) {
       const bool ha = i < na - ia, hb = i < nb - ib;
       ms.a_key[i] = ha ? A.key[ia + i] : ~0ull;
-      ms.a_coef[i] = ha ? (uint32_t)(((uint64_t)A.coef[ia + i] * A.scale) % p) : 0u;
+      ms.a_coef[i] = ha ? (A.coef[ia + i] * A.scale) % p : 0u;
       ms.b_key[i] = hb ? Bd.key[ib + i] : ~0ull;
-      ms.b_coef[i] = hb ? (uint32_t)(((uint64_t)Bd.coef[ib + i] * Bd.scale) % p) : 0u;
+      ms.b_coef[i] = hb ? (Bd.coef[ib + i] * Bd.scale) % p : 0u;
     }
     __syncthreads();
     const uint32_t q0 = 2 * tid < nout ? 2 * tid : nout;
@@ -1694,7 +1699,7 @@ __device__ bool block_merge_small(const RedState& s, unsigned char* raw, MergeRe
     while (e >= pre + q.d[r].len) pre += q.d[r++].len;
     const RunDesc& R = q.d[r];
     sk[e] = R.key[e - pre];
-    sc[e] = R.scale == 1 ? R.coef[e - pre] : (uint32_t)(((uint64_t)R.coef[e - pre] * R.scale) % p);
+    sc[e] = R.scale == 1 ? R.coef[e - pre] : (R.coef[e - pre] * R.scale) % p;
   }
   __syncthreads();
   for (uint32_t e = tid; e < total; e += blockDim.x) {
@@ -1799,7 +1804,7 @@ __device__ uint32_t chunk_merge(MergeReq& q, unsigned char* raw, const uint32_t*
     const RunDesc& R = q.d[r];
     const uint32_t i = lo[r] + e - q.roff[r];
     sk[e] = R.key[i];
-    sc[e] = R.scale == 1 ? R.coef[i] : (uint32_t)(((uint64_t)R.coef[i] * R.scale) % p);
+    sc[e] = R.scale == 1 ? R.coef[i] : (R.coef[i] * R.scale) % p;
   }
   __syncthreads();
   const uint32_t per = (total + blockDim.x - 1) / blockDim.x;
@@ -2063,31 +2068,62 @@ __device__ __forceinline__ void ring_new(const Rings& R, RingRun& r, int lane, i
 }
 
 // Pivot of the ring runs: the smallest head key with a nonzero combined
-// coefficient; heads at a key whose coefficients cancel move on.
-__device__ __forceinline__ uint64_t ring_pivot(const Rings& R, RingRun& r, int lane, uint32_t p, uint32_t* coef_out) {
+// coefficient; heads at a key whose coefficients cancel move on.  One step is a
+// 64-bit warp minimum and one warp sum that carries both the number of heads at
+// the minimum and the number of those whose ring runs out when they move on;
+// over Z/2 (Z2, compiled separately: the general loop is much slower) an odd
+// count is a nonzero coefficient, so the step needs no other collective, and
+// the heads advance without a divergent branch.
+template <bool Z2>
+__device__ __forceinline__ uint64_t ring_pivot(const Rings& R, RingRun& rs, int lane, uint32_t p,
+                                                uint32_t* coef_out) {
+  RingRun r = rs;  // the search works on registers; the chain's copy may live in local memory
   for (;;) {
     const uint64_t m = warp_min_u64(r.hk);
     if (m == ~0ull) {
+      rs = r;
       *coef_out = 0;
       return IDX_NONE;
     }
     const bool at = r.hk == m;
-    const uint32_t c = warp_coef_sum(at, r.hc, p);
+    const bool refill = at && r.cur + 1 < r.len && r.cur + 1 >= r.wend;
+    uint32_t c;
+    if (Z2) {
+      const uint32_t sum = __reduce_add_sync(0xffffffffu, at ? 1u + (refill ? 0x10000u : 0u) : 0u);
+      if (sum & 1u) {
+        rs = r;
+        *coef_out = 1u;
+        return m;
+      }
+      c = sum >> 16;  // runs to refill
+    } else {
+      const uint32_t cs = __reduce_add_sync(0xffffffffu, at ? r.hc : 0u) % p;
+      if (cs) {
+        rs = r;
+        *coef_out = cs;
+        return m;
+      }
+      c = __popc(__ballot_sync(0xffffffffu, refill));
+    }
+    r.cur += at ? 1u : 0u;
     if (c) {
-      *coef_out = c;
-      return m;
+      unsigned need = __ballot_sync(0xffffffffu, refill);
+      while (need) {
+        const int L = __ffs(need) - 1;
+        need &= need - 1;
+        ring_load(R, r, lane, L, Z2 ? 2u : p);
+      }
     }
-    if (at) ++r.cur;
-    unsigned need = __ballot_sync(0xffffffffu, at && r.cur < r.len && r.cur >= r.wend);
-    while (need) {
-      const int L = __ffs(need) - 1;
-      need &= need - 1;
-      ring_load(R, r, lane, L, p);
-    }
-    if (at) {
-      const uint32_t x = r.slot * RING_W + (r.cur & (RING_W - 1));
-      r.hk = r.cur < r.len ? R.k[x] : ~0ull;
-      r.hc = r.cur < r.len ? scaled(R.c[x], r.scale, p) : 0u;
+    const uint32_t x = r.slot * RING_W + (r.cur & (RING_W - 1));
+    const uint64_t nk = R.k[x];
+    if (Z2) {
+      if (at) r.hk = r.cur < r.len ? nk : ~0ull;
+    } else {
+      const uint32_t nc = R.c[x];
+      if (at) {
+        r.hk = r.cur < r.len ? nk : ~0ull;
+        r.hc = r.cur < r.len ? (nc * r.scale) % p : 0u;
+      }
     }
   }
 }
@@ -2157,7 +2193,7 @@ __device__ __forceinline__ void chainb_add(const DimArgs& a, const RedState& s, 
     atomicAdd(s.added, (unsigned long long)wn);
     if ((ch.step & 15) == 0) atomicAdd(s.heartbeat, 1u);  // progress, for the grid barrier
   }
-  ch.key = ring_pivot(R, ch.r, lane, a.p, &ch.coef);
+  ch.key = a.p == 2 ? ring_pivot<true>(R, ch.r, lane, a.p, &ch.coef) : ring_pivot<false>(R, ch.r, lane, a.p, &ch.coef);
   ch.owner = -1;
 }
 
