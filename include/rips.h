@@ -129,6 +129,36 @@ RIPS_API int rips_barcodes_packed(const float* d_packed, int64_t n, int32_t layo
                                   float threshold, uint32_t p, void* cuda_stream, rips_result_t** out);
 
 /*
+ * rips_barcodes_sparse -- the barcode of a sparse distance matrix (Section 4,
+ * "Input": a sparse matrix, where a missing entry is an infinite distance),
+ * without any n x n array: memory grows with the number of edges, not with n^2.
+ * d_i, d_j, d_len: m entries in DEVICE memory (read only, owned by the caller),
+ * entry e the edge {d_i[e], d_j[e]} of length d_len[e]; 0 <= i, j < n, i != j,
+ * each unordered pair at most once, lengths finite and >= 0 (else
+ * RIPS_ERR_BAD_ARG).  Entries longer than the threshold are left out; with no
+ * threshold (+inf or NaN) every entry is kept (the enclosing radius does not
+ * apply).  n at most 92681.  Rank lookups search the sorted neighbour lists
+ * instead of reading a rank matrix.  Every filtration key must still fit in 64
+ * bits (diameter rank bits + simplex index bits; RIPS_ERR_OVERFLOW otherwise),
+ * which bounds n at a given density and dimension.  Statuses and the result as
+ * for rips_barcodes_device.
+ */
+RIPS_API int rips_barcodes_sparse(const int32_t* d_i, const int32_t* d_j, const float* d_len, int64_t m, int64_t n,
+                                  int32_t dim_max, float threshold, uint32_t p, void* cuda_stream,
+                                  rips_result_t** out);
+
+/*
+ * rips_barcodes_sparse_points -- the same for a point cloud (n points of k FP32
+ * coordinates, DEVICE, row-major) and a finite threshold: the pairs within the
+ * threshold are found on the device tile by tile (distances by the rule of
+ * rips_distance_matrix_device) and only they are kept.  An infinite or NaN
+ * threshold is RIPS_ERR_BAD_ARG (the cloud would be dense).  The result feeds
+ * rips_barcodes_backward with the same points.
+ */
+RIPS_API int rips_barcodes_sparse_points(const float* d_points, int64_t n, int32_t k, int32_t dim_max,
+                                         float threshold, uint32_t p, void* cuda_stream, rips_result_t** out);
+
+/*
  * rips_distance_matrix_device -- the finite metric space of a point cloud
  * (Section 4 "Input" accepts point clouds as well as distance matrices):
  * Euclidean distances of n points with k FP32

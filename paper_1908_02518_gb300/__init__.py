@@ -20,7 +20,7 @@ import numpy as np
 from . import _lib
 from ._lib import RipsError
 
-__all__ = ["barcodes", "barcodes_packed", "barcodes_batched", "barcodes_batched_dists", "distance_matrix", "backward",
+__all__ = ["barcodes", "barcodes_packed", "barcodes_sparse", "barcodes_sparse_points", "barcodes_batched", "barcodes_batched_dists", "distance_matrix", "backward",
            "backward_dist", "Result", "RipsError",
            "RipsBarcodes", "launch_count", "set_kernel_timing", "BAR_DTYPE"]
 
@@ -149,6 +149,44 @@ def barcodes_packed(packed, n: int, layout: str = "lower", dim_max: int = 1, thr
     st = lib.rips_barcodes_packed(C.c_void_p(t.data_ptr() if t.numel() else 0), n, code, dim_max,
                                   C.c_float(threshold), p, _stream_ptr(stream), C.byref(out))
     _lib.check(st, "rips_barcodes_packed")
+    return _collect(lib, out, keep_handle)
+
+
+def barcodes_sparse(i, j, length, n: int, dim_max: int = 1, threshold: float = math.inf, p: int = 2, stream=None,
+                    keep_handle: bool = False) -> Result:
+    """Barcodes of a sparse distance matrix given as (i, j, length) entries
+    (each unordered pair once; missing pairs are infinitely far), with no n x n
+    array anywhere.  Host arrays are copied to the device."""
+    import torch
+    lib = _lib.load()
+    ti = torch.as_tensor(np.asarray(i, dtype=np.int32) if not hasattr(i, "is_cuda") else i).to(torch.int32).cuda()
+    tj = torch.as_tensor(np.asarray(j, dtype=np.int32) if not hasattr(j, "is_cuda") else j).to(torch.int32).cuda()
+    tl = torch.as_tensor(np.asarray(length, dtype=np.float32) if not hasattr(length, "is_cuda") else length)
+    tl = tl.to(torch.float32).cuda()
+    m = ti.numel()
+    if tj.numel() != m or tl.numel() != m:
+        raise ValueError("i, j and length must have the same length")
+    out = C.c_void_p()
+    st = lib.rips_barcodes_sparse(C.c_void_p(ti.data_ptr() if m else 0), C.c_void_p(tj.data_ptr() if m else 0),
+                                  C.c_void_p(tl.data_ptr() if m else 0), m, n, dim_max, C.c_float(threshold), p,
+                                  _stream_ptr(stream), C.byref(out))
+    _lib.check(st, "rips_barcodes_sparse")
+    return _collect(lib, out, keep_handle)
+
+
+def barcodes_sparse_points(points, threshold: float, dim_max: int = 1, p: int = 2, stream=None,
+                           keep_handle: bool = False) -> Result:
+    """Barcodes of a point cloud ((n, k) FP32 CUDA tensor) at a finite
+    threshold, keeping only the pairs within it (no n x n array)."""
+    import torch
+    lib = _lib.load()
+    x = points.contiguous()
+    if not x.is_cuda or x.dtype != torch.float32 or x.dim() != 2:
+        raise ValueError("points must be an (n, k) float32 CUDA tensor")
+    out = C.c_void_p()
+    st = lib.rips_barcodes_sparse_points(C.c_void_p(x.data_ptr()), x.shape[0], x.shape[1], dim_max,
+                                         C.c_float(threshold), p, _stream_ptr(stream), C.byref(out))
+    _lib.check(st, "rips_barcodes_sparse_points")
     return _collect(lib, out, keep_handle)
 
 

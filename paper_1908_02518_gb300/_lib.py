@@ -42,7 +42,7 @@ class Tuning(C.Structure):
 # every symbol declared in include/rips.h
 EXPORTS = [
     "rips_barcodes", "rips_barcodes_device", "rips_distance_matrix_device", "rips_barcodes_batched",
-    "rips_barcodes_backward", "rips_barcodes_packed", "rips_barcodes_batched_dists", "rips_barcodes_backward_dist", "rips_result_num_bars", "rips_result_bars", "rips_result_num_clouds",
+    "rips_barcodes_backward", "rips_barcodes_packed", "rips_barcodes_sparse", "rips_barcodes_sparse_points", "rips_barcodes_batched_dists", "rips_barcodes_backward_dist", "rips_result_num_bars", "rips_result_bars", "rips_result_num_clouds",
     "rips_result_dim_max", "rips_result_threshold", "rips_result_stats", "rips_result_phase_ms",
     "rips_result_free", "rips_status_string", "rips_kernel_launch_count", "rips_set_kernel_timing",
     "rips_result_kernel_ms", "rips_h0_barcode_noalloc", "rips_set_tuning", "rips_get_tuning", "rips_clear_tuning",
@@ -80,6 +80,10 @@ def load(build_if_missing: bool = True):
     lib.rips_barcodes_batched.restype = C.c_int
     lib.rips_barcodes_backward.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp]
     lib.rips_barcodes_backward.restype = C.c_int
+    lib.rips_barcodes_sparse.argtypes = [vp, vp, vp, i64, i64, i32, C.c_float, u32, vp, pres]
+    lib.rips_barcodes_sparse.restype = C.c_int
+    lib.rips_barcodes_sparse_points.argtypes = [vp, i64, i32, i32, C.c_float, u32, vp, pres]
+    lib.rips_barcodes_sparse_points.restype = C.c_int
     lib.rips_barcodes_packed.argtypes = [vp, i64, i32, i32, C.c_float, u32, vp, pres]
     lib.rips_barcodes_packed.restype = C.c_int
     lib.rips_barcodes_batched_dists.argtypes = [C.POINTER(vp), C.POINTER(C.c_int64), i32, i32, C.c_float, u32, vp,

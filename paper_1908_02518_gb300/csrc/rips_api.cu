@@ -99,6 +99,7 @@ struct Workspace {
   Buf amk[2];  // apparent-pair maps of dimensions d and d - 1 ((key, value) pairs)
   Buf bars, bars_alt, bk0, bk1, bp0, bp1, bartmp, nbars;
   Buf stats, bwd_bars, bwd_off, cdist, clouds, tileoff, vcloud, ccounts;
+  Buf nrank, nkey, nkey_alt, nval, nval_alt, cursor;  // neighbour lists of a sparse input
   size_t r_cap = 0;
   HostPinned* pinned = nullptr;
   cudaEvent_t tev[16] = {};
@@ -296,11 +297,24 @@ int sync_read(Workspace& w, cudaStream_t s) {
 
 int bits_of_count(uint64_t count) { return std::max(1, bit_width64(count ? count - 1 : 0)); }
 
+// One cloud given by its edges only (no n x n matrix): a list of (i, j,
+// length) entries, or a point cloud whose pairs within the threshold are found
+// on the device.
+struct SparseIn {
+  const int32_t* ei = nullptr;
+  const int32_t* ej = nullptr;
+  const float* len = nullptr;
+  uint64_t m = 0;
+  const float* pts = nullptr;
+  int k = 0;
+};
+
 // The whole barcode pipeline for a batch of clouds whose n_c x n_c distance
-// matrices lie back to back at dD.  Bars are left in w.bars (device), with the
-// statistics, thresholds and timings in `out`.
+// matrices lie back to back at dD -- or, with `sp`, for one cloud given by its
+// edges, which never forms an n x n array.  Bars are left in w.bars (device),
+// with the statistics, thresholds and timings in `out`.
 int run_batch(Workspace& w, const float* dD, const std::vector<int64_t>& ns, int dim_max, float threshold,
-              uint32_t p, cudaStream_t s, BatchOut& out) {
+              uint32_t p, cudaStream_t s, BatchOut& out, const SparseIn* sp = nullptr) {
   HostPinned* hp = w.pinned;
   const int C = (int)ns.size();
   const int kmax = dim_max + 2;
@@ -331,6 +345,14 @@ int run_batch(Workspace& w, const float* dD, const std::vector<int64_t>& ns, int
     tiles += nb * (nb + 1) / 2;
   }
   tile_off[C] = (uint32_t)tiles;
+  if (sp) {  // a sparse input: no matrix, and the edge list's room is what the input needs
+    if (C != 1) return RIPS_ERR_BAD_ARG;
+    RR = 0;
+    tiles = 0;
+    e_cap = sp->pts ? std::min<uint64_t>(e_cap, 64ull * (uint64_t)n_max + 1024) : std::max<uint64_t>(sp->m, 1);
+    const float t = (std::isnan(threshold) || std::isinf(threshold)) ? INFINITY : threshold;
+    ci[0].t_eff = t;
+  }
   if (N > 0xFFFFFFF0ull || e_cap > 0xFFFFFFF0ull || tiles > 0x7FFFFFFFull) return RIPS_ERR_OVERFLOW;
   const int cb = C > 1 ? bit_width64((uint64_t)C - 1) : 0;
   const int eb = bits_of_count(host_binom(n_max, 2));
@@ -354,21 +376,48 @@ int run_batch(Workspace& w, const float* dD, const std::vector<int64_t>& ns, int
   CK(cudaMemsetAsync(w.err.p, 0, 16, s));
   CK(cudaMemsetAsync(w.ecount.p, 0, 16, s));
   CK(cudaMemsetAsync(w.ccounts.p, 0, (size_t)(C + 1) * 4, s));
-  {
-    KTimer kt(w, RIPS_K_PROLOGUE, s);
-    CK(launch_cloud_vertices(dclouds, C, P<uint32_t>(w.vcloud), s));
-    CK(launch_validate_rowmax(dD, dclouds, P<uint32_t>(w.tileoff), C, (uint32_t)tiles, P<uint32_t>(w.rowmax),
-                              P<uint32_t>(w.err), s));
-    CK(launch_threshold(P<uint32_t>(w.rowmax), dclouds, C, threshold, s));
-    CK(launch_edge_keys(dD, dclouds, P<uint32_t>(w.vcloud), (uint32_t)N, eb, P<uint64_t>(w.ekeys),
-                        P<uint32_t>(w.ecount), P<uint32_t>(w.ccounts), (uint32_t)e_cap, s));
-  }
   std::vector<uint32_t> ccount(C);
-  CK(cudaMemcpyAsync(&hp->u32[0], w.ecount.p, 4, cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(&hp->u32[1], w.err.p, 4, cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(ccount.data(), w.ccounts.p, (size_t)C * 4, cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(ci.data(), dclouds, (size_t)C * sizeof(CloudInfo), cudaMemcpyDeviceToHost, s));
-  CR(sync_read(w, s));
+  if (!sp) {
+    {
+      KTimer kt(w, RIPS_K_PROLOGUE, s);
+      CK(launch_cloud_vertices(dclouds, C, P<uint32_t>(w.vcloud), s));
+      CK(launch_validate_rowmax(dD, dclouds, P<uint32_t>(w.tileoff), C, (uint32_t)tiles, P<uint32_t>(w.rowmax),
+                                P<uint32_t>(w.err), s));
+      CK(launch_threshold(P<uint32_t>(w.rowmax), dclouds, C, threshold, s));
+      CK(launch_edge_keys(dD, dclouds, P<uint32_t>(w.vcloud), (uint32_t)N, eb, P<uint64_t>(w.ekeys),
+                          P<uint32_t>(w.ecount), P<uint32_t>(w.ccounts), (uint32_t)e_cap, s));
+    }
+    CK(cudaMemcpyAsync(&hp->u32[0], w.ecount.p, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&hp->u32[1], w.err.p, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ccount.data(), w.ccounts.p, (size_t)C * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ci.data(), dclouds, (size_t)C * sizeof(CloudInfo), cudaMemcpyDeviceToHost, s));
+    CR(sync_read(w, s));
+  } else {
+    // the edges within the threshold, grown and listed again if the room was short
+    for (int attempt = 0; attempt < 8; ++attempt) {
+      {
+        KTimer kt(w, RIPS_K_PROLOGUE, s);
+        CK(launch_cloud_vertices(dclouds, C, P<uint32_t>(w.vcloud), s));
+        if (sp->pts)
+          CK(launch_point_edges(sp->pts, n_max, sp->k, ci[0].t_eff, eb, P<uint64_t>(w.ekeys), P<uint32_t>(w.ecount),
+                                (uint32_t)e_cap, s));
+        else
+          CK(launch_coo_edge_keys(sp->ei, sp->ej, sp->len, sp->m, n_max, ci[0].t_eff, eb, P<uint64_t>(w.ekeys),
+                                  P<uint32_t>(w.ecount), (uint32_t)e_cap, P<uint32_t>(w.err), s));
+      }
+      CK(cudaMemcpyAsync(&hp->u32[0], w.ecount.p, 4, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(&hp->u32[1], w.err.p, 4, cudaMemcpyDeviceToHost, s));
+      CR(sync_read(w, s));
+      if (hp->u32[1] & ERRF_BAD_INPUT) return RIPS_ERR_BAD_ARG;
+      if (hp->u32[0] <= e_cap) break;
+      e_cap = hp->u32[0];
+      CR(ensure(w.ekeys, e_cap * 8));
+      CR(ensure(w.ekeys_alt, e_cap * 8));
+      CK(cudaMemsetAsync(w.ecount.p, 0, 16, s));
+    }
+    if (hp->u32[0] > e_cap) return RIPS_ERR_INTERNAL;
+    ccount[0] = hp->u32[0];
+  }
   if (hp->u32[1] & ERRF_BAD_INPUT) return RIPS_ERR_BAD_ARG;
   const uint32_t m = hp->u32[0];
   out.t_eff.resize(C);
@@ -396,17 +445,23 @@ int run_batch(Workspace& w, const float* dD, const std::vector<int64_t>& ns, int
   CR(ensure(w.eflags, (size_t)(m + 1) * 4));
   CR(ensure(w.erank, (size_t)(m + 1) * 4));
   CR(ensure(w.rvalue, (size_t)(m + 1) * 4));
-  CR(ensure(w.R, RR * 4));
+  if (!sp) CR(ensure(w.R, RR * 4));
   CR(ensure(w.deg, (size_t)(N + 2) * 4));
   {
     KTimer kt(w, RIPS_K_PROLOGUE, s);
     CK(launch_assign_ranks(keys, m, eb, P<uint32_t>(w.eflags), (uint32_t*)w.sorttmp.p, P<uint32_t>(w.erank),
                            P<float>(w.rvalue), &P<uint32_t>(w.ecount)[1], s));
-    CK(cudaMemsetAsync(w.R.p, 0xFF, RR * 4, s));
-    CK(launch_fill_rank_matrix(keys, P<uint32_t>(w.erank), m, eb, dclouds, P<uint32_t>(w.R), s));
     CK(cudaMemsetAsync(w.deg.p, 0, (size_t)(N + 2) * 4, s));
-    CK(launch_neighbor_counts(P<uint32_t>(w.R), dclouds, P<uint32_t>(w.vcloud), (uint32_t)N, P<uint32_t>(w.deg),
-                              &P<uint32_t>(w.ecount)[3], s));
+    if (!sp) {
+      CK(cudaMemsetAsync(w.R.p, 0xFF, RR * 4, s));
+      CK(launch_fill_rank_matrix(keys, P<uint32_t>(w.erank), m, eb, dclouds, P<uint32_t>(w.R), s));
+      CK(launch_neighbor_counts(P<uint32_t>(w.R), dclouds, P<uint32_t>(w.vcloud), (uint32_t)N, P<uint32_t>(w.deg),
+                                &P<uint32_t>(w.ecount)[3], s));
+    } else {
+      CK(cudaMemsetAsync((char*)w.ecount.p + 12, 0, 4, s));
+      CK(launch_sparse_degrees(keys, m, eb, P<uint32_t>(w.deg), s));
+      CK(launch_max(P<uint32_t>(w.deg), (uint32_t)N, &P<uint32_t>(w.ecount)[3], s));
+    }
     CK(launch_exclusive_scan(P<uint32_t>(w.deg), P<uint32_t>(w.deg), (uint32_t)N + 1, w.sorttmp.p,
                              &P<uint32_t>(w.ecount)[2], s));
   }
@@ -415,9 +470,29 @@ int run_batch(Workspace& w, const float* dD, const std::vector<int64_t>& ns, int
   const uint32_t num_ranks = hp->u32[2];
   const uint32_t nbr_total = hp->u32[3];
   const uint32_t max_deg = hp->u32[4];
-  CR(ensure(w.nbr, (size_t)nbr_total * 4));
+  CR(ensure(w.nbr, (size_t)nbr_total * 4 + 4));
   CR(ensure(w.binom, (size_t)(kmax + 1) * (n_max + 1) * 8));
-  {
+  if (sp) {  // both directions of every edge with its rank, sorted into decreasing neighbour order
+    const uint32_t q = nbr_total;
+    CR(ensure(w.nrank, (size_t)q * 4 + 4));
+    CR(ensure(w.nkey, (size_t)q * 8 + 8));
+    CR(ensure(w.nkey_alt, (size_t)q * 8 + 8));
+    CR(ensure(w.nval, (size_t)q * 4 + 4));
+    CR(ensure(w.nval_alt, (size_t)q * 4 + 4));
+    CR(ensure(w.cursor, (size_t)N * 4 + 4));
+    CR(ensure(w.sorttmp, std::max(w.sorttmp.cap, sort_temp_bytes(q))));
+    KTimer kt(w, RIPS_K_PROLOGUE, s);
+    CK(cudaMemsetAsync(w.cursor.p, 0, (size_t)N * 4, s));
+    CK(launch_sparse_fill(keys, P<uint32_t>(w.erank), m, eb, P<uint32_t>(w.deg), P<uint32_t>(w.cursor),
+                          P<uint64_t>(w.nkey), P<uint32_t>(w.nval), s));
+    bool nalt = false;
+    CK(radix_sort_u64(P<uint64_t>(w.nkey), P<uint64_t>(w.nkey_alt), P<uint32_t>(w.nval), P<uint32_t>(w.nval_alt), q,
+                      32 + bit_width64((uint64_t)n_max), w.sorttmp.p, w.sorttmp.cap, &nalt, s));
+    CK(launch_sparse_unpack(nalt ? P<uint64_t>(w.nkey_alt) : P<uint64_t>(w.nkey),
+                            nalt ? P<uint32_t>(w.nval_alt) : P<uint32_t>(w.nval), q, P<uint32_t>(w.nbr),
+                            P<uint32_t>(w.nrank), s));
+    CK(launch_binomial_table(P<uint64_t>(w.binom), n_max, kmax, s));
+  } else {
     KTimer kt(w, RIPS_K_PROLOGUE, s);
     CK(launch_neighbor_fill(P<uint32_t>(w.R), dclouds, P<uint32_t>(w.vcloud), (uint32_t)N, P<uint32_t>(w.deg),
                             P<uint32_t>(w.nbr), s));
@@ -472,9 +547,10 @@ int run_batch(Workspace& w, const float* dD, const std::vector<int64_t>& ns, int
     a.d = d;
     a.nclouds = C;
     a.clouds = dclouds;
-    a.R = P<uint32_t>(w.R);
+    a.R = sp ? nullptr : P<uint32_t>(w.R);
     a.nbr_off = P<uint32_t>(w.deg);
     a.nbr = P<uint32_t>(w.nbr);
+    a.nrank = sp ? P<uint32_t>(w.nrank) : nullptr;
     a.binom = P<uint64_t>(w.binom);
     a.bn = n_max;
     a.kmax = kmax;
@@ -789,6 +865,42 @@ int barcodes_locked(Workspace& w, const float* dD, int64_t n, int32_t dim_max, f
   r->point_offsets = {0, n};
   index_result(r);
   *out = r;
+  return RIPS_OK;
+}
+
+// one cloud given by its edges (SparseIn): the barcode without an n x n array
+int sparse_locked(Workspace& w, const SparseIn& sp, int64_t n, int32_t dim_max, float threshold, uint32_t p,
+                  cudaStream_t s, rips_result_t** out) {
+  rips_result* r = new (std::nothrow) rips_result();
+  if (!r) return RIPS_ERR_OOM;
+  r->clouds = 1;
+  r->dim_max = dim_max;
+  r->k = sp.pts ? sp.k : 0;
+  BatchOut bo;
+  std::vector<int64_t> ns{n};
+  int rc = run_batch(w, nullptr, ns, dim_max, threshold, p, s, bo, &sp);
+  if (rc == RIPS_OK) {
+    const int sbits = std::max(1, bit_width64(host_binom((uint64_t)n, dim_max + 1)));
+    rc = finish_bars(w, bo.nbars, sbits, 0, s, r->bars);
+  }
+  if (rc != RIPS_OK) {
+    delete r;
+    return rc;
+  }
+  fill_result(r, bo);
+  r->npoints.push_back(n);
+  r->point_offsets = {0, n};
+  index_result(r);
+  *out = r;
+  return RIPS_OK;
+}
+
+// sparse inputs: vertex ids and edge indices stay within 32 and 64 bits
+int check_sparse_args(int64_t n, int32_t dim_max, float threshold, uint32_t p) {
+  if (n < 1 || n > 92681 || dim_max < 0 || dim_max > MAX_DIM - 1) return RIPS_ERR_BAD_ARG;
+  if (!std::isnan(threshold) && threshold < 0.0f) return RIPS_ERR_BAD_ARG;
+  if (!is_prime(p) || p >= 65536) return RIPS_ERR_BAD_MODULUS;
+  if (host_binom((uint64_t)n, dim_max + 2) >= (1ull << 63)) return RIPS_ERR_OVERFLOW;
   return RIPS_OK;
 }
 
@@ -1130,6 +1242,7 @@ int plan_create(PlanState& pl, const int64_t* offsets, int32_t batch, int32_t k,
   a.R = P<uint32_t>(w.R);
   a.nbr_off = P<uint32_t>(w.deg);
   a.nbr = P<uint32_t>(w.nbr);
+  a.nrank = nullptr;
   a.binom = P<uint64_t>(w.binom);
   a.err = P<uint32_t>(w.err);
   a.amap = P<uint64_t>(w.amk[0]);
@@ -1360,6 +1473,49 @@ RIPS_API int rips_barcodes_packed(const float* d_packed, int64_t n, int32_t layo
     CR(ensure(w->dist, (size_t)n * n * 4));
     CK(launch_unpack_triangle(d_packed, (int)n, layout == RIPS_UPPER_TRIANGLE, P<float>(w->dist), s));
     return barcodes_locked(*w, P<float>(w->dist), n, dim_max, threshold, p, s, out);
+  } catch (...) {
+    return RIPS_ERR_INTERNAL;
+  }
+}
+
+RIPS_API int rips_barcodes_sparse(const int32_t* d_i, const int32_t* d_j, const float* d_len, int64_t m, int64_t n,
+                                  int32_t dim_max, float threshold, uint32_t p, void* cuda_stream,
+                                  rips_result_t** out) {
+  if (!out) return RIPS_ERR_BAD_ARG;
+  *out = nullptr;
+  if (m < 0 || (m > 0 && (!d_i || !d_j || !d_len)) || (uint64_t)m > 0xFFFFFFF0ull) return RIPS_ERR_BAD_ARG;
+  int rc = check_sparse_args(n, dim_max, threshold, p);
+  if (rc != RIPS_OK) return rc;
+  try {
+    Workspace* w = current_workspace();
+    if (!w) return RIPS_ERR_OOM;
+    std::lock_guard<std::mutex> g(w->mu);
+    SparseIn sp;
+    sp.ei = d_i;
+    sp.ej = d_j;
+    sp.len = d_len;
+    sp.m = (uint64_t)m;
+    return sparse_locked(*w, sp, n, dim_max, threshold, p, (cudaStream_t)cuda_stream, out);
+  } catch (...) {
+    return RIPS_ERR_INTERNAL;
+  }
+}
+
+RIPS_API int rips_barcodes_sparse_points(const float* d_points, int64_t n, int32_t k, int32_t dim_max,
+                                         float threshold, uint32_t p, void* cuda_stream, rips_result_t** out) {
+  if (!out) return RIPS_ERR_BAD_ARG;
+  *out = nullptr;
+  if (!d_points || k < 1 || !(threshold >= 0.0f) || std::isinf(threshold)) return RIPS_ERR_BAD_ARG;
+  int rc = check_sparse_args(n, dim_max, threshold, p);
+  if (rc != RIPS_OK) return rc;
+  try {
+    Workspace* w = current_workspace();
+    if (!w) return RIPS_ERR_OOM;
+    std::lock_guard<std::mutex> g(w->mu);
+    SparseIn sp;
+    sp.pts = d_points;
+    sp.k = k;
+    return sparse_locked(*w, sp, n, dim_max, threshold, p, (cudaStream_t)cuda_stream, out);
   } catch (...) {
     return RIPS_ERR_INTERNAL;
   }

@@ -90,16 +90,34 @@ __device__ __forceinline__ Binom stage_binom(const DimArgs& a, uint64_t* smem) {
 // ---------------------------------------------------------------- clouds
 // A cloud's view: its size, rank matrix and neighbour-list offsets (indexed by
 // local vertex) into the shared list array.
+// R is null for a sparse input: the rank of an edge then comes from the
+// neighbour lists (nrank[q] = rank of the edge to nbr[q]).
 struct CV {
   int n;
   const uint32_t* R;
   const uint32_t* off;
   const uint32_t* nbr;
+  const uint32_t* nrank;
 };
 
 __device__ __forceinline__ CV cloud_view(const DimArgs& a, uint32_t c) {
   const CloudInfo ci = a.clouds[c];
-  return CV{ci.n, a.R + ci.roff, a.nbr_off + ci.voff, a.nbr};
+  return CV{ci.n, a.R ? a.R + ci.roff : nullptr, a.nbr_off + ci.voff, a.nbr, a.nrank};
+}
+
+// Rank of the edge (x, y), RANK_INF when it is above the threshold or x == y:
+// one read of the rank matrix, or with a sparse input a binary search for y in
+// x's neighbour list (vertices in decreasing order).
+__device__ __forceinline__ uint32_t rank_of(const CV& cv, int x, int y) {
+  if (cv.R) return cv.R[(size_t)x * cv.n + y];
+  const uint32_t end = cv.off[x + 1];
+  uint32_t lo = cv.off[x], hi = end;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (cv.nbr[mid] > (uint32_t)y) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo < end && cv.nbr[lo] == (uint32_t)y ? cv.nrank[lo] : RANK_INF;
 }
 
 __device__ __forceinline__ uint64_t low_mask(int bits) { return bits >= 64 ? ~0ull : ((1ull << bits) - 1); }
@@ -159,12 +177,11 @@ __device__ __forceinline__ void decode(const Binom& B, int n, uint64_t N, int d,
 }
 
 // rank of sigma with vertex v[l] removed, for every l (d >= 1)
-__device__ __forceinline__ void ranks_minus_one(const uint32_t* __restrict__ R, int n, const int* v, int d,
-                                                uint32_t* out) {
+__device__ __forceinline__ void ranks_minus_one(const CV& cv, const int* v, int d, uint32_t* out) {
   for (int l = 0; l <= d; ++l) out[l] = 0;
   for (int a = 0; a <= d; ++a)
     for (int b = a + 1; b <= d; ++b) {
-      uint32_t r = R[(size_t)v[a] * n + v[b]];
+      uint32_t r = rank_of(cv, v[a], v[b]);
       for (int l = 0; l <= d; ++l)
         if (l != a && l != b) out[l] = max(out[l], r);
     }
@@ -215,7 +232,7 @@ __device__ __forceinline__ bool cofacet_of(const CV& cv, const Binom& B, const i
   int c = 0;
   bool ok = true;
   for (int l = 0; l <= d; ++l) {  // no early exit: the loads are independent
-    const uint32_t x = cv.R[(size_t)v[l] * cv.n + j];
+    const uint32_t x = rank_of(cv, v[l], j);
     ok &= x != RANK_INF;
     r = max(r, x);
     c += v[l] > j;
@@ -256,7 +273,7 @@ __device__ int first_equal_cofacet(const CV& cv, const int* v, int d, uint32_t s
       j = (int)cv.nbr[q];
       hit = true;
       for (int l = 0; l <= d; ++l) {
-        uint32_t x = cv.R[(size_t)v[l] * cv.n + j];
+        uint32_t x = rank_of(cv, v[l], j);
         rj[l] = x;
         if (x > srank) hit = false;  // also rejects RANK_INF and j in sigma
       }
@@ -303,7 +320,7 @@ __device__ int zero_apparent_facet(const CV& cv, const int* w, int k, uint32_t r
       above = u > drop;
       if (above) {
         hit = true;
-        for (int x = 0; x < k; ++x) hit &= cv.R[(size_t)rv[x] * cv.n + u] <= r;
+        for (int x = 0; x < k; ++x) hit &= rank_of(cv, rv[x], u) <= r;
         // u is not a vertex of tau: the dropped vertex is excluded by u > drop, the
         // others by R = RANK_INF on the diagonal
       }
@@ -416,7 +433,7 @@ __global__ void __launch_bounds__(256) enumerate_kernel(DimArgs a, const uint64_
       uint32_t r = r0;
       if (ok)
         for (int l = 0; l < d; ++l) {
-          uint32_t x = cv.R[(size_t)v[l] * cv.n + j];
+          uint32_t x = rank_of(cv, v[l], j);
           if (x == RANK_INF) {
             ok = false;
             break;
@@ -519,7 +536,7 @@ __global__ void __launch_bounds__(256) test_kernel(DimArgs a, const uint64_t* __
       int app = 0;
       if (lane == hl) {
         uint32_t minus[MAX_DIM + 2];
-        ranks_minus_one(cv.R, cv.n, v, d, minus);
+        ranks_minus_one(cv, v, d, minus);
         app = 1;
         // facets of tau dropping a vertex above j come before sigma in index order
         for (int l = 0; l <= d && v[l] > j; ++l) {
@@ -557,7 +574,7 @@ __global__ void __launch_bounds__(256) test_kernel(DimArgs a, const uint64_t* __
         fac = pair_find(a.pmap, a.pmap_mask, g, &unused);
       } else {
         uint32_t minus[MAX_DIM + 2];
-        ranks_minus_one(cv.R, cv.n, v, d, minus);
+        ranks_minus_one(cv, v, d, minus);
         fac = zero_apparent_facet(cv, v, d, r, minus, lane) >= 0;
       }
       if (fac) {
@@ -665,7 +682,7 @@ __device__ uint64_t pivot_apparent_facet(const DimArgs& a, const CV& cv, const B
   int w[MAX_DIM + 2];
   decode(B, cv.n, tidx, k, w);
   uint32_t minus[MAX_DIM + 2];
-  ranks_minus_one(cv.R, cv.n, w, k, minus);
+  ranks_minus_one(cv, w, k, minus);
   int l = zero_apparent_facet(cv, w, k, tr, minus, lane);
   if (l < 0) return IDX_NONE;
   // facet index: drop w[l]; vertices above it keep C(w, k+1-pos) -> C(w, k-pos)

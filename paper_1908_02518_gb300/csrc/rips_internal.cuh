@@ -135,6 +135,19 @@ cudaError_t launch_neighbor_counts(const uint32_t* R, const CloudInfo* clouds, c
 cudaError_t launch_neighbor_fill(const uint32_t* R, const CloudInfo* clouds, const uint32_t* vcloud, uint32_t nverts,
                                  const uint32_t* off, uint32_t* nbr, cudaStream_t s);
 cudaError_t launch_distance_matrix(const float* pts, int n, int k, float* D, cudaStream_t s);
+// sparse inputs (one cloud): edge keys of a (i, j, length) list or of a point
+// cloud's pairs within t, appended at *count (capacity cap; the count may
+// exceed cap, nothing past it is written); neighbour lists with ranks
+cudaError_t launch_coo_edge_keys(const int32_t* ei, const int32_t* ej, const float* len, uint64_t m, int n, float t,
+                                 int eb, uint64_t* keys, uint32_t* count, uint32_t cap, uint32_t* err, cudaStream_t s);
+cudaError_t launch_point_edges(const float* pts, int n, int k, float t, int eb, uint64_t* keys, uint32_t* count,
+                               uint32_t cap, cudaStream_t s);
+cudaError_t launch_sparse_degrees(const uint64_t* keys, uint32_t m, int eb, uint32_t* deg, cudaStream_t s);
+cudaError_t launch_sparse_fill(const uint64_t* keys, const uint32_t* erank, uint32_t m, int eb, const uint32_t* off,
+                               uint32_t* cursor, uint64_t* nkey, uint32_t* nval, cudaStream_t s);
+cudaError_t launch_sparse_unpack(const uint64_t* nkey, const uint32_t* nval, uint32_t q, uint32_t* nbr,
+                                 uint32_t* nrank, cudaStream_t s);
+cudaError_t launch_max(const uint32_t* x, uint32_t n, uint32_t* out, cudaStream_t s);
 // packed strict triangle (lower: row by row from row 1; upper: row by row to row n-2) -> strict lower triangle of D
 cudaError_t launch_unpack_triangle(const float* packed, int n, int upper, float* D, cudaStream_t s);
 cudaError_t launch_pad_past_count(uint64_t* keys, const uint32_t* count, uint64_t cap, cudaStream_t s);
@@ -159,9 +172,10 @@ struct DimArgs {
   int d;                           // columns are d-simplices
   int nclouds;
   const CloudInfo* clouds;
-  const uint32_t* R;               // rank matrices of all clouds
+  const uint32_t* R;               // rank matrices of all clouds (null for a sparse input)
   const uint32_t* nbr_off;         // neighbour-list CSR over all clouds' vertices (global rows)
   const uint32_t* nbr;             // local vertex ids, decreasing within a row
+  const uint32_t* nrank;           // sparse input: rank of the edge to each nbr entry (else null)
   const uint64_t* binom;           // binomial table for n_max, stride bn + 1
   int bn;
   int kmax;                        // rows 0..kmax of the table are staged

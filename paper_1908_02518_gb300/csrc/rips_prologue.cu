@@ -304,6 +304,133 @@ __global__ void distance_multi_kernel(const float* __restrict__ pts, int k, cons
   }
 }
 
+// ---------------------------------------------------------------- sparse inputs
+// A sparse input never forms the n x n matrix: its edges (length <= threshold)
+// are listed as keys like edge_keys_kernel's, and the neighbour lists carry the
+// rank of each edge (Section 4: sparse distance matrices, where a missing entry
+// is an infinite distance).
+
+// one edge key, the same layout as edge_keys_kernel (single cloud)
+__device__ __forceinline__ uint64_t edge_key(int i, int j, float x, int eb) {
+  const int a = i > j ? i : j, b = i > j ? j : i;
+  const uint64_t emask = (1ull << eb) - 1;
+  const uint64_t idx = (uint64_t)a * (a - 1) / 2 + (uint64_t)b;
+  return ((uint64_t)__float_as_uint(x == 0.0f ? 0.0f : x) << eb) | (emask - idx);
+}
+
+// warp-aggregated append of the lanes' keys where `ok` holds
+__device__ __forceinline__ void append_key(bool ok, uint64_t key, uint64_t* keys, uint32_t* count, uint32_t cap) {
+  const int lane = threadIdx.x & 31;
+  const unsigned m = __ballot_sync(0xffffffffu, ok);
+  if (!m) return;
+  uint32_t base = 0;
+  if (lane == 0) base = atomicAdd(count, (uint32_t)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (ok) {
+    const uint32_t pos = base + __popc(m & ((1u << lane) - 1u));
+    if (pos < cap) keys[pos] = key;
+  }
+}
+
+// a list of (i, j, length) entries, each unordered pair at most once
+__global__ void coo_edge_keys_kernel(const int32_t* __restrict__ ei, const int32_t* __restrict__ ej,
+                                     const float* __restrict__ len, uint64_t m, int n, float t, int eb,
+                                     uint64_t* __restrict__ keys, uint32_t* __restrict__ count, uint32_t cap,
+                                     uint32_t* __restrict__ err) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t first = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (uint64_t e0 = first - (threadIdx.x & 31); e0 < m; e0 += stride) {  // whole warps iterate together
+    const uint64_t e = e0 + (threadIdx.x & 31);
+    bool ok = false;
+    uint64_t key = 0;
+    if (e < m) {
+      const int i = ei[e], j = ej[e];
+      const float x = len[e];
+      const bool valid = i >= 0 && i < n && j >= 0 && j < n && i != j && x >= 0.0f && !isinf(x);
+      if (!valid) set_error(err, ERRF_BAD_INPUT);
+      ok = valid && x <= t;
+      if (ok) key = edge_key(i, j, x, eb);
+    }
+    append_key(ok, key, keys, count, cap);
+  }
+}
+
+// the edges of a point cloud within the threshold, distances by the rule of
+// distance_kernel, one 32 x 32 tile of (i > j) pairs per block (8 rows a warp)
+__global__ void point_edges_kernel(const float* __restrict__ pts, int n, int k, float t, int eb,
+                                   uint64_t* __restrict__ keys, uint32_t* __restrict__ count, uint32_t cap) {
+  uint32_t I, J;  // tile row and column, I >= J
+  {
+    const uint64_t b = blockIdx.x;
+    uint32_t r = (uint32_t)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+    while ((uint64_t)r * (r + 1) / 2 > b) --r;
+    while ((uint64_t)(r + 1) * (r + 2) / 2 <= b) ++r;
+    I = r;
+    J = (uint32_t)(b - (uint64_t)r * (r + 1) / 2);
+  }
+  const int j = (int)(J * 32 + (threadIdx.x & 31));
+  for (int rr = threadIdx.x >> 5; rr < 32; rr += blockDim.x >> 5) {
+    const int i = (int)(I * 32 + rr);
+    bool ok = false;
+    float x = 0.0f;
+    if (i < n && j < i) {
+      double acc = 0.0;
+      for (int c = 0; c < k; ++c) {
+        const double diff = __dsub_rn((double)pts[(size_t)i * k + c], (double)pts[(size_t)j * k + c]);
+        acc = __dadd_rn(acc, __dmul_rn(diff, diff));
+      }
+      x = __double2float_rn(__dsqrt_rn(acc));
+      ok = x <= t;
+    }
+    append_key(ok, ok ? edge_key(i, j, x, eb) : 0ull, keys, count, cap);
+  }
+}
+
+// degrees from the sorted edge keys
+__global__ void sparse_degree_kernel(const uint64_t* __restrict__ keys, uint32_t m, int eb, uint32_t* __restrict__ deg) {
+  const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m) return;
+  const uint64_t emask = (1ull << eb) - 1;
+  int a, b;
+  edge_vertices(emask - (keys[e] & emask), &a, &b);
+  atomicAdd(&deg[a], 1u);
+  atomicAdd(&deg[b], 1u);
+}
+
+// both directions of every edge, keyed (vertex, complement of the neighbour) so
+// that one sort leaves each list in decreasing neighbour order, with the rank
+__global__ void sparse_fill_kernel(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ erank, uint32_t m,
+                                   int eb, const uint32_t* __restrict__ off, uint32_t* __restrict__ cursor,
+                                   uint64_t* __restrict__ nkey, uint32_t* __restrict__ nval) {
+  const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m) return;
+  const uint64_t emask = (1ull << eb) - 1;
+  int a, b;
+  edge_vertices(emask - (keys[e] & emask), &a, &b);
+  const uint32_t r = erank[e];
+  const uint32_t pa = off[a] + atomicAdd(&cursor[a], 1u);
+  nkey[pa] = ((uint64_t)a << 32) | (0xFFFFFFFFu - (uint32_t)b);
+  nval[pa] = r;
+  const uint32_t pb = off[b] + atomicAdd(&cursor[b], 1u);
+  nkey[pb] = ((uint64_t)b << 32) | (0xFFFFFFFFu - (uint32_t)a);
+  nval[pb] = r;
+}
+
+__global__ void sparse_unpack_kernel(const uint64_t* __restrict__ nkey, const uint32_t* __restrict__ nval, uint32_t q,
+                                     uint32_t* __restrict__ nbr, uint32_t* __restrict__ nrank) {
+  const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= q) return;
+  nbr[e] = 0xFFFFFFFFu - (uint32_t)(nkey[e] & 0xFFFFFFFFull);
+  nrank[e] = nval[e];
+}
+
+__global__ void max_kernel(const uint32_t* __restrict__ x, uint32_t n, uint32_t* __restrict__ out) {
+  uint32_t m = 0;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) m = max(m, x[i]);
+  m = __reduce_max_sync(0xffffffffu, m);
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
 }  // namespace
 
 cudaError_t launch_binomial_table(uint64_t* tab, int n, int kmax, cudaStream_t s) {
@@ -418,6 +545,57 @@ cudaError_t launch_unpack_triangle(const float* packed, int n, int upper, float*
   if (n < 2) return cudaSuccess;
   dim3 blk(32, 8), grd((n + 31) / 32, (n + 7) / 8);
   unpack_triangle_kernel<<<grd, blk, 0, s>>>(packed, n, upper, D);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coo_edge_keys(const int32_t* ei, const int32_t* ej, const float* len, uint64_t m, int n, float t,
+                                 int eb, uint64_t* keys, uint32_t* count, uint32_t cap, uint32_t* err, cudaStream_t s) {
+  if (m == 0) return cudaSuccess;
+  uint64_t blocks = (m + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  coo_edge_keys_kernel<<<(unsigned)blocks, 256, 0, s>>>(ei, ej, len, m, n, t, eb, keys, count, cap, err);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_point_edges(const float* pts, int n, int k, float t, int eb, uint64_t* keys, uint32_t* count,
+                               uint32_t cap, cudaStream_t s) {
+  if (n < 2) return cudaSuccess;
+  const uint64_t nb = ((uint64_t)n + 31) / 32;
+  point_edges_kernel<<<(unsigned)(nb * (nb + 1) / 2), 256, 0, s>>>(pts, n, k, t, eb, keys, count, cap);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sparse_degrees(const uint64_t* keys, uint32_t m, int eb, uint32_t* deg, cudaStream_t s) {
+  if (m == 0) return cudaSuccess;
+  sparse_degree_kernel<<<(m + 255) / 256, 256, 0, s>>>(keys, m, eb, deg);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sparse_fill(const uint64_t* keys, const uint32_t* erank, uint32_t m, int eb, const uint32_t* off,
+                               uint32_t* cursor, uint64_t* nkey, uint32_t* nval, cudaStream_t s) {
+  if (m == 0) return cudaSuccess;
+  sparse_fill_kernel<<<(m + 255) / 256, 256, 0, s>>>(keys, erank, m, eb, off, cursor, nkey, nval);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sparse_unpack(const uint64_t* nkey, const uint32_t* nval, uint32_t q, uint32_t* nbr,
+                                 uint32_t* nrank, cudaStream_t s) {
+  if (q == 0) return cudaSuccess;
+  sparse_unpack_kernel<<<(q + 255) / 256, 256, 0, s>>>(nkey, nval, q, nbr, nrank);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_max(const uint32_t* x, uint32_t n, uint32_t* out, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  uint32_t blocks = (n + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  max_kernel<<<blocks, 256, 0, s>>>(x, n, out);
   note_launch();
   return cudaGetLastError();
 }

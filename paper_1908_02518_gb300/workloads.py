@@ -132,6 +132,17 @@ def sphere_points(n: int, seed: int, k: int = 4) -> np.ndarray:
     return _unit_vectors(rng, n, k).astype(np.float32)
 
 
+def clifford_points(n: int, seed: int) -> np.ndarray:
+    """Points uniform on the Clifford torus S^1(1/sqrt 2) x S^1(1/sqrt 2) in R^4
+    (the torus4 data set of the paper's experiments is such a sample): two
+    independent uniform unit vectors of R^2, scaled by 1/sqrt 2."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    u = _unit_vectors(rng, n, 2)
+    v = _unit_vectors(rng, n, 2)
+    s = 1.0 / np.sqrt(2.0)
+    return (np.concatenate([u, v], axis=1) * s).astype(np.float32)
+
+
 def circle_points(rng: np.random.Generator, n: int, sigma: float = 0.05) -> np.ndarray:
     a = _unit_vectors(rng, n, 2)
     pts = np.stack([a[:, 0], a[:, 1], np.zeros(n)], axis=1)
@@ -195,6 +206,18 @@ def sphere3_192() -> Workload:
                     "192 points uniform on S^3 in R^4, full Rips, H0-H3, Z/3")
 
 
+def clifford_1500() -> Workload:
+    return Workload("clifford1500", clifford_points(1500, 1006), 2, 0.4, 2,
+                    "1500 points on the Clifford torus in R^4, threshold 0.4, H0-H2, Z/2 (sparse path)")
+
+
+def clifford(n: int, threshold: float, dim_max: int, seed: int = 1007) -> Workload:
+    """The torus4 configuration of the paper (n = 50,000, t = 0.15) or a smaller
+    one at the same average degree: t = 0.15 sqrt(50000 / n)."""
+    return Workload(f"clifford{n}", clifford_points(n, seed), dim_max, threshold, 2,
+                    f"{n} points on the Clifford torus in R^4, threshold {threshold}, H0-H{dim_max}, Z/2 (sparse path)")
+
+
 def batch_clouds(count: int = 256, lo: int = 64, hi: int = 512, meta_seed: int = 4000,
                  cloud_seed: int = 40000) -> list[np.ndarray]:
     """Ragged list of FP32 point clouds (circle / torus / cube mix)."""
@@ -220,6 +243,7 @@ WORKLOADS = {
     "torus1000": torus_1000,
     "so3_4096": so3_4096,
     "s3_192": sphere3_192,
+    "clifford1500": clifford_1500,
 }
 
 

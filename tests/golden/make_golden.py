@@ -121,4 +121,4 @@ def main(names):
 
 
 if __name__ == "__main__":
-    main(sys.argv[1:] or ["cube100", "torus1000", "so3_4096", "s3_192", "batch"])
+    main(sys.argv[1:] or ["cube100", "torus1000", "so3_4096", "s3_192", "clifford1500", "batch"])
