@@ -238,6 +238,15 @@ namespace {
     if (_r != RIPS_OK) return _r; \
   } while (0)
 
+// Bits per vertex when the d + 1 vertices of a d-simplex of a cloud of at most
+// n_max points fit in 60 bits (the pair map's values then carry them, so the
+// reduction need not decode the facet's index), else 0.
+int packed_vertex_bits(int n_max, int d) {
+  int b = 1;
+  while (b < 31 && (1ll << b) < (long long)n_max) ++b;
+  return (d + 1) * b <= 60 ? b : 0;
+}
+
 bool is_prime(uint32_t p) {
   if (p < 2) return false;
   for (uint32_t q = 2; (uint64_t)q * q <= p; ++q)
@@ -563,6 +572,7 @@ int run_batch(Workspace& w, const float* dD, const std::vector<int64_t>& ns, int
     a.err = P<uint32_t>(w.err);
     a.amap = nullptr;
     a.amap_mask = 0;
+    a.vbits = 0;
     a.pmap = prev_amap;
     a.pmap_mask = prev_amask;
     {
@@ -625,6 +635,7 @@ int run_batch(Workspace& w, const float* dD, const std::vector<int64_t>& ns, int
       CK(cudaMemsetAsync(w.amk[cur].p, 0xFF, (size_t)acap * 16, s));
       a.amap = P<uint64_t>(w.amk[cur]);
       a.amap_mask = acap - 1;
+      a.vbits = packed_vertex_bits(n_max, d);
     }
     {
       KTimer kt(w, RIPS_K_APPARENT, s);
@@ -1261,6 +1272,7 @@ int plan_create(PlanState& pl, const int64_t* offsets, int32_t batch, int32_t k,
   a.err = P<uint32_t>(w.err);
   a.amap = P<uint64_t>(w.amk[0]);
   a.amap_mask = pl.acap - 1;
+  a.vbits = packed_vertex_bits(pl.n_max, 1);
   pl.blocks = reduction_blocks(a, (uint32_t)E);
   if (pl.blocks < 1) return RIPS_ERR_CUDA;
   return RIPS_OK;

@@ -176,6 +176,18 @@ __device__ __forceinline__ void decode(const Binom& B, int n, uint64_t N, int d,
   }
 }
 
+// Vertices of a d-simplex given by a reference: its index, or (packed) its
+// vertices packed vbits apiece as the pair map stores them.
+__device__ __forceinline__ void simplex_vertices(const Binom& B, int n, uint64_t ref, bool packed, int vbits, int d,
+                                                 int* v) {
+  if (!packed) {
+    decode(B, n, ref, d, v);
+    return;
+  }
+  const uint64_t m = (1ull << vbits) - 1;
+  for (int l = 0; l <= d; ++l) v[l] = (int)((ref >> (l * vbits)) & m);
+}
+
 // rank of sigma with vertex v[l] removed, for every l (d >= 1)
 __device__ __forceinline__ void ranks_minus_one(const CV& cv, const int* v, int d, uint32_t* out) {
   for (int l = 0; l <= d; ++l) out[l] = 0;
@@ -560,7 +572,14 @@ __global__ void __launch_bounds__(256) test_kernel(DimArgs a, const uint64_t* __
           const uint64_t tidx = cs.above[c] + B(j, d + 2 - c) + cs.below[c];
           const int64_t slot = pair_insert(a.amap, a.amap_mask, table_key(a, cl, tidx));
           if (slot < 0) set_error(a.err, ERRF_TABLE_FULL);
-          else a.amap[2 * slot + 1] = (idx << 4) | (uint64_t)c;
+          else {
+            uint64_t ref = idx;
+            if (a.vbits) {
+              ref = 0;
+              for (int l = 0; l <= d; ++l) ref |= (uint64_t)v[l] << (l * a.vbits);
+            }
+            a.amap[2 * slot + 1] = (ref << 4) | (uint64_t)c;
+          }
         }
         continue;
       }
@@ -665,8 +684,10 @@ __device__ void min_entry(const DimArgs& a, const CV& cv, const Binom& B, int la
   *out_coef = best == IDX_NONE ? 0 : sum;
 }
 
-// Apparent facet of the pivot row tau (a (d+1)-simplex): returns the facet index
-// (IDX_NONE if none), its rank and the coefficient of tau in its coboundary.
+// Apparent facet of the pivot row tau (a (d+1)-simplex): returns the facet's
+// reference (IDX_NONE if none; packed vertices when the pair map holds them,
+// see DimArgs::vbits, else its index), its rank and the coefficient of tau in
+// its coboundary.
 __device__ uint64_t pivot_apparent_facet(const DimArgs& a, const CV& cv, const Binom& B, int lane, uint32_t cl,
                                          uint64_t key, uint32_t* frank, uint32_t* tcoef) {
   const int k = a.d + 1;
@@ -702,7 +723,8 @@ __device__ uint64_t pivot_apparent_facet(const DimArgs& a, const CV& cv, const B
 
 // Owner of the pivot row `key` of a column of cloud cl: the zero apparent facet
 // of the row (Section 4, "Persistence pairs": apparent pairs are not in the
-// table), else the table's owner (0xFFFFFFFF: none).  With the recorded pair
+// table; its reference as pivot_apparent_facet gives it), else the table's
+// owner (0xFFFFFFFF: none).  With the recorded pair
 // map the two lookups run at once on lanes 0 and 1.  Warp-cooperative; every
 // lane gets the results.
 __device__ __forceinline__ uint64_t pivot_owner(const DimArgs& a, const RedState& s, const CV& cv, const Binom& B,
@@ -717,22 +739,30 @@ __device__ __forceinline__ uint64_t pivot_owner(const DimArgs& a, const RedState
   if (a.amap) {
     // lane 0 probes the pair map, lane 1 the pivot table, with the same load
     // instructions, so the two lookups take the time of one
+    // (each probe loads the slot's value with its key)
     uint64_t val = 0;
     int found = 0;
     if (lane < 2) {
       const uint64_t mask = lane == 0 ? a.amap_mask : s.t_mask;
       uint64_t h = mix(tkey) & mask;
       for (uint64_t probe = 0; probe <= mask; ++probe) {
-        const uint64_t* kp = lane == 0 ? a.amap + 2 * h : s.t_keys + h;
-        const uint64_t cur = *kp;
+        uint64_t cur, cv2;
+        if (lane == 0) {
+          const ulonglong2 e = *reinterpret_cast<const ulonglong2*>(a.amap + 2 * h);
+          cur = e.x;
+          cv2 = e.y;
+        } else {
+          cur = s.t_keys[h];
+          cv2 = s.t_vals[h];
+        }
         if (cur == tkey) {
           found = 1;
+          val = cv2;
           break;
         }
         if (cur == IDX_NONE) break;
         h = (h + 1) & mask;
       }
-      if (found) val = lane == 0 ? a.amap[2 * h + 1] : (uint64_t)s.t_vals[h];
     }
     const int ffound = __shfl_sync(0xffffffffu, found, 0);
     const uint64_t v = __shfl_sync(0xffffffffu, val, 0);
@@ -762,13 +792,15 @@ __device__ __forceinline__ uint64_t pivot_owner(const DimArgs& a, const RedState
 // scratch slice and sorted there.
 
 // all cofacets of the d-simplex (idx, rank) with their paper-orientation signs,
-// unsorted, into buf; returns the count (warp-uniform)
+// unsorted, into buf; returns the count (warp-uniform).  idx is a reference as
+// simplex_vertices takes it.
 __device__ uint32_t gen_coboundary(const DimArgs& a, const CV& cv, const Binom& B, int lane, uint64_t idx,
-                                   uint32_t rank, uint32_t scale, uint64_t* bkey, uint32_t* bcoef, uint32_t cap) {
+                                   bool packed, uint32_t rank, uint32_t scale, uint64_t* bkey, uint32_t* bcoef,
+                                   uint32_t cap) {
   const int d = a.d;
   const unsigned lt = (1u << lane) - 1u;
   int v[MAX_DIM + 2];
-  decode(B, cv.n, idx, d, v);
+  simplex_vertices(B, cv.n, idx, packed, a.vbits, d, v);
   CofacetSums cs;
   cofacet_sums(B, v, d, cs);
   const int av = v[min_degree_vertex(cv, v, d + 1)];
@@ -972,11 +1004,11 @@ struct SortTile {
 // coboundary of the d-simplex (idx, rank), generated, sorted (in the warp's
 // shared-memory tile when it fits) and stored in the arena
 __device__ bool gen_sorted(const DimArgs& a, const RedState& s, const CV& cv, const Binom& B, int lane,
-                           const SortTile& tile, uint64_t idx, uint32_t rank, const uint64_t** k, const uint32_t** c,
-                           uint32_t* n) {
+                           const SortTile& tile, uint64_t idx, bool packed, uint32_t rank, const uint64_t** k,
+                           const uint32_t** c, uint32_t* n) {
   unsigned long long off;
   if (s.scr_slice <= SORT_TILE) {
-    const uint32_t cnt = gen_coboundary(a, cv, B, lane, idx, rank, 1u, tile.key, tile.coef, SORT_TILE);
+    const uint32_t cnt = gen_coboundary(a, cv, B, lane, idx, packed, rank, 1u, tile.key, tile.coef, SORT_TILE);
     __syncwarp();
     warp_sort_pairs(tile.key, tile.coef, cnt, lane);
     if (!arena_alloc(s, lane, cnt ? cnt : 1, &off)) return false;
@@ -993,7 +1025,7 @@ __device__ bool gen_sorted(const DimArgs& a, const RedState& s, const CV& cv, co
   if (!arena_alloc(s, lane, s.scr_slice, &off)) return false;
   uint64_t* kk = s.r_key + off;
   uint32_t* cc = s.r_coef + off;
-  const uint32_t cnt = gen_coboundary(a, cv, B, lane, idx, rank, 1u, kk, cc, s.scr_slice);
+  const uint32_t cnt = gen_coboundary(a, cv, B, lane, idx, packed, rank, 1u, kk, cc, s.scr_slice);
   __syncwarp();
   warp_sort_pairs(kk, cc, cnt, lane);
   *k = kk;
@@ -1120,8 +1152,9 @@ enum : int { CH_DONE = 0, CH_MERGE = 1, CH_ARENA = 2, CH_LONG = 3, CH_INTERNAL =
 // work handed from warp 0 to its block: runs to merge, or a coboundary to generate
 struct ChainReq {
   unsigned mask;  // CH_MERGE: lanes of the runs
-  uint64_t gidx;  // CH_GEN, CH_GEN_SELF: the simplex
+  uint64_t gidx;  // CH_GEN, CH_GEN_SELF: the simplex (a reference as simplex_vertices takes it)
   uint32_t grank;
+  bool gpacked;
 };
 
 // R_j <- R_j - lambda C, lambda = pivot coefficient ratio (Algorithm 1): the run
@@ -1184,7 +1217,7 @@ __device__ int chain_advance(const DimArgs& a, const RedState& s, const CV& cv, 
         ch.owner = k;
         continue;
       }
-      if (!gen_sorted(a, s, cv, B, lane, tile, fidx, frank, &wk, &wc, &wn)) return CH_ARENA;
+      if (!gen_sorted(a, s, cv, B, lane, tile, fidx, a.vbits != 0, frank, &wk, &wc, &wn)) return CH_ARENA;
       wcoef = tcoef;
     } else {
       const uint32_t k = (uint32_t)ch.owner;
@@ -1197,7 +1230,7 @@ __device__ int chain_advance(const DimArgs& a, const RedState& s, const CV& cv, 
         uint64_t kidx;
         uint32_t kr, kcl;
         column_simplex(a, s, k, &kidx, &kr, &kcl);
-        if (!gen_sorted(a, s, cv, B, lane, tile, kidx, kr, &wk, &wc, &wn)) return CH_ARENA;
+        if (!gen_sorted(a, s, cv, B, lane, tile, kidx, false, kr, &wk, &wc, &wn)) return CH_ARENA;
       }
     }
     // the working column's own entries, on first use
@@ -1208,7 +1241,7 @@ __device__ int chain_advance(const DimArgs& a, const RedState& s, const CV& cv, 
       if (jn) {
         jk = s.r_key + s.r_off[j];
         jc = s.r_coef + s.r_off[j];
-      } else if (!gen_sorted(a, s, cv, B, lane, tile, jidx, jrank, &jk, &jc, &jn)) {
+      } else if (!gen_sorted(a, s, cv, B, lane, tile, jidx, false, jrank, &jk, &jc, &jn)) {
         return CH_ARENA;
       }
       if (lane == 0) ch.r = make_run(jk, jc, jn, 1, a.p);
@@ -1431,8 +1464,9 @@ struct MergeReq {
   uint32_t n;
   unsigned mask;
   int state;
-  uint64_t gidx;  // simplex whose coboundary is to be generated
+  uint64_t gidx;  // simplex whose coboundary is to be generated (a reference as simplex_vertices takes it)
   uint32_t grank;
+  bool gpacked;
   uint32_t wsum[WARPS_PER_BLOCK];
   uint32_t roff[33];  // run offsets of a merge staged in shared memory
   unsigned long long off;
@@ -1492,12 +1526,12 @@ __device__ void block_bitonic(uint64_t* key, uint32_t* coef, uint32_t n2) {
 // sorted copy in shared memory (null when the sort ran in the arena).  Called by
 // the whole block; false (in every thread) when the arena is full.
 __device__ bool block_gen_sorted(const DimArgs& a, const RedState& s, const CV& cv, const Binom& B,
-                                 unsigned char* raw, MergeReq& q, uint64_t idx, uint32_t rank, RunDesc* out,
-                                 const uint64_t** sk, const uint32_t** sc) {
+                                 unsigned char* raw, MergeReq& q, uint64_t idx, bool packed, uint32_t rank,
+                                 RunDesc* out, const uint64_t** sk, const uint32_t** sc) {
   const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int d = a.d;
   int v[MAX_DIM + 2];
-  decode(B, cv.n, idx, d, v);
+  simplex_vertices(B, cv.n, idx, packed, a.vbits, d, v);
   CofacetSums cs;
   cofacet_sums(B, v, d, cs);
   const int av = v[min_degree_vertex(cv, v, d + 1)];
@@ -2026,7 +2060,9 @@ struct RingRun {
   const uint32_t* coef;
   uint32_t len, cur, scale;
   uint64_t hk;    // head key, ~0 once the run is used up
+  uint64_t nk;    // the key after the head (~0 past the end)
   uint32_t hc;    // head coefficient times scale, mod p
+  uint32_t nc;    // and the next one's
   uint32_t wend;  // the ring holds entries [wend - RING_W, wend) of the run (entry i at i mod RING_W)
   uint32_t slot;
 };
@@ -2037,15 +2073,16 @@ __device__ __forceinline__ RingRun ring_empty() {
   r.coef = nullptr;
   r.len = r.cur = r.wend = 0;
   r.scale = 1;
-  r.hk = ~0ull;
-  r.hc = 0;
+  r.hk = r.nk = ~0ull;
+  r.hc = r.nc = 0;
   r.slot = 0;
   return r;
 }
 
 // Warp-wide: lane L's run (its fields set, cursor at cur) loads entries
 // [cur, cur + RING_W) into its ring, from the shared-memory copy (sk, sc;
-// indexed like the run) when there is one, and takes its head.
+// indexed like the run) when there is one, and takes its head and the entry
+// after it.
 __device__ __forceinline__ void ring_load(const Rings& R, RingRun& r, int lane, int L, uint32_t p,
                                           const uint64_t* sk = nullptr, const uint32_t* sc = nullptr) {
   const uint64_t* kp = (const uint64_t*)__shfl_sync(0xffffffffu, (unsigned long long)r.key, L);
@@ -2063,8 +2100,11 @@ __device__ __forceinline__ void ring_load(const Rings& R, RingRun& r, int lane, 
   if (lane == L) {
     r.wend = min(base + RING_W, len);
     const uint32_t at = r.slot * RING_W + (r.cur & (RING_W - 1));
+    const uint32_t nx = r.slot * RING_W + ((r.cur + 1) & (RING_W - 1));
     r.hk = r.cur < r.len ? R.k[at] : ~0ull;
     r.hc = r.cur < r.len ? scaled(R.c[at], r.scale, p) : 0u;
+    r.nk = r.cur + 1 < r.len ? R.k[nx] : ~0ull;
+    r.nc = r.cur + 1 < r.len ? scaled(R.c[nx], r.scale, p) : 0u;
   }
 }
 
@@ -2086,44 +2126,58 @@ __device__ __forceinline__ void ring_new(const Rings& R, RingRun& r, int lane, i
 
 // Pivot of the ring runs: the smallest head key with a nonzero combined
 // coefficient; heads at a key whose coefficients cancel move on.  One step is a
-// 64-bit warp minimum and one warp sum that carries both the number of heads at
-// the minimum and the number of those whose ring runs out when they move on;
-// over Z/2 (Z2, compiled separately: the general loop is much slower) an odd
-// count is a nonzero coefficient, so the step needs no other collective, and
-// the heads advance without a divergent branch.
+// 64-bit warp minimum and one warp sum that carries both the coefficient sum
+// (over Z/2, compiled separately, the number) of the heads at the minimum and
+// the number of those whose ring runs dry when they move on.  The search is
+// pipelined: every lane keeps the entry after its head in registers and reads
+// the one after that from its ring at the start of a step, and the next
+// minimum, on the assumption that the heads at this one cancel, is taken while
+// the sum is still under way, so a step costs about one minimum.
 template <bool Z2>
 __device__ __forceinline__ uint64_t ring_pivot(const Rings& R, RingRun& rs, int lane, uint32_t p,
                                                 uint32_t* coef_out) {
   RingRun r = rs;  // the search works on registers; the chain's copy may live in local memory
+  uint64_t m = warp_min_u64(r.hk);
   for (;;) {
-    const uint64_t m = warp_min_u64(r.hk);
     if (m == ~0ull) {
       rs = r;
       *coef_out = 0;
       return IDX_NONE;
     }
+    const uint32_t x = r.slot * RING_W + ((r.cur + 2) & (RING_W - 1));
+    const uint64_t nn = R.k[x];  // meaningful if it is in the ring (else the ring is refilled below)
     const bool at = r.hk == m;
-    const bool refill = at && r.cur + 1 < r.len && r.cur + 1 >= r.wend;
-    uint32_t c;
+    const uint32_t c1 = r.cur + 1;    // the head's index once this lane moves on
+    const bool more = c1 + 1 < r.len;  // and an entry follows it
+    const bool refill = at && more && c1 + 1 >= r.wend;
+    const uint32_t sum = Z2 ? __reduce_add_sync(0xffffffffu, at ? 1u + (refill ? 0x10000u : 0u) : 0u)
+                            : __reduce_add_sync(0xffffffffu, at ? r.hc + (refill ? 0x1000000u : 0u) : 0u);
+    const uint64_t hk2 = at ? r.nk : r.hk;
+    const uint64_t m2 = warp_min_u64(hk2);
+    const uint64_t nk2 = at ? (more ? nn : ~0ull) : r.nk;
+    uint32_t cs;
     if (Z2) {
-      const uint32_t sum = __reduce_add_sync(0xffffffffu, at ? 1u + (refill ? 0x10000u : 0u) : 0u);
-      if (sum & 1u) {
-        rs = r;
-        *coef_out = 1u;
-        return m;
-      }
-      c = sum >> 16;  // runs to refill
+      cs = sum & 1u;
     } else {
-      const uint32_t cs = __reduce_add_sync(0xffffffffu, at ? r.hc : 0u) % p;
-      if (cs) {
-        rs = r;
-        *coef_out = cs;
-        return m;
-      }
-      c = __popc(__ballot_sync(0xffffffffu, refill));
+      cs = (sum & 0xFFFFFFu) % p;  // at most 32 (p - 1) < 2^21
     }
-    r.cur += at ? 1u : 0u;
-    if (c) {
+    if (cs) {
+      rs = r;
+      *coef_out = cs;
+      return m;
+    }
+    if (Z2) {
+      r.cur = at ? c1 : r.cur;
+      r.hk = hk2;
+      r.nk = nk2;
+    } else if (at) {
+      r.cur = c1;
+      r.hk = hk2;
+      r.nk = nk2;
+      r.hc = r.nc;
+      r.nc = more ? scaled(R.c[x], r.scale, p) : 0u;
+    }
+    if (sum >> (Z2 ? 16 : 24)) {  // refill the rings that ran dry (the head stays; the entry after it is reloaded)
       unsigned need = __ballot_sync(0xffffffffu, refill);
       while (need) {
         const int L = __ffs(need) - 1;
@@ -2131,17 +2185,7 @@ __device__ __forceinline__ uint64_t ring_pivot(const Rings& R, RingRun& rs, int 
         ring_load(R, r, lane, L, Z2 ? 2u : p);
       }
     }
-    const uint32_t x = r.slot * RING_W + (r.cur & (RING_W - 1));
-    const uint64_t nk = R.k[x];
-    if (Z2) {
-      if (at) r.hk = r.cur < r.len ? nk : ~0ull;
-    } else {
-      const uint32_t nc = R.c[x];
-      if (at) {
-        r.hk = r.cur < r.len ? nk : ~0ull;
-        r.hc = r.cur < r.len ? (nc * r.scale) % p : 0u;
-      }
-    }
+    m = m2;
   }
 }
 
@@ -2157,7 +2201,9 @@ __device__ __forceinline__ void ring_pack(RingRun& r, int lane, int* nr) {
   t.cur = __shfl_sync(0xffffffffu, r.cur, src);
   t.scale = __shfl_sync(0xffffffffu, r.scale, src);
   t.hk = __shfl_sync(0xffffffffu, r.hk, src);
+  t.nk = __shfl_sync(0xffffffffu, r.nk, src);
   t.hc = __shfl_sync(0xffffffffu, r.hc, src);
+  t.nc = __shfl_sync(0xffffffffu, r.nc, src);
   t.wend = __shfl_sync(0xffffffffu, r.wend, src);
   t.slot = __shfl_sync(0xffffffffu, r.slot, src);
   r = lane < cnt ? t : ring_empty();
@@ -2239,6 +2285,7 @@ __device__ int chainb_advance(const DimArgs& a, const RedState& s, const CV& cv,
       if (!jn) {
         req->gidx = jidx;
         req->grank = jrank;
+        req->gpacked = false;
         return CH_GEN_SELF;
       }
       ring_new(R, ch.r, lane, 0, 0, s.r_key + s.r_off[j], s.r_coef + s.r_off[j], jn, 1, a.p);
@@ -2255,6 +2302,7 @@ __device__ int chainb_advance(const DimArgs& a, const RedState& s, const CV& cv,
       }
       req->gidx = fidx;
       req->grank = frank;
+      req->gpacked = a.vbits != 0;
       ch.pcoef = tcoef;
       return CH_GEN;
     }
@@ -2267,6 +2315,7 @@ __device__ int chainb_advance(const DimArgs& a, const RedState& s, const CV& cv,
       column_simplex(a, s, k, &kidx, &kr, &kcl);
       req->gidx = kidx;
       req->grank = kr;
+      req->gpacked = false;
       ch.pcoef = wcoef;
       return CH_GEN;
     }
@@ -2323,7 +2372,7 @@ __device__ void reduce_one_block(const DimArgs& a, const RedState& s, const Bino
   int state = CH_DONE;
   for (;;) {
     if (tid < 32) {
-      ChainReq cr{0u, 0ull, 0u};
+      ChainReq cr{0u, 0ull, 0u, false};
       int st = CH_DONE;
       if (!finishing) st = chainb_advance(a, s, cv, B, R, lane, j, cl, ch, &cr, jidx, jr);
       if (st == CH_DONE && !finishing) {  // the chain ended: R_j must become one run
@@ -2347,6 +2396,7 @@ __device__ void reduce_one_block(const DimArgs& a, const RedState& s, const Bino
         q.state = st;
         q.gidx = cr.gidx;
         q.grank = cr.grank;
+        q.gpacked = cr.gpacked;
       }
     }
     __syncthreads();
@@ -2375,7 +2425,7 @@ __device__ void reduce_one_block(const DimArgs& a, const RedState& s, const Bino
       RunDesc g;
       const uint64_t* gk;
       const uint32_t* gc;
-      if (!block_gen_sorted(a, s, cv, B, raw, q, q.gidx, q.grank, &g, &gk, &gc)) {
+      if (!block_gen_sorted(a, s, cv, B, raw, q, q.gidx, q.gpacked, q.grank, &g, &gk, &gc)) {
         state = CH_ARENA;
         break;
       }

@@ -189,11 +189,13 @@ struct DimArgs {
   // zero-persistence apparent pairs (sigma, tau) with sigma a d-simplex, written
   // by the test kernel: a hash table of (key, value) pairs, slot h at amap[2h]
   // and amap[2h + 1] (one 16-byte load reads both), amap_mask + 1 slots; key
-  // (cloud << row_bits) | idx(tau), value (idx(sigma) << 4) | position of the
-  // vertex tau has beyond sigma; null when col_bits > 60 (the index does not
-  // fit beside the position)
+  // (cloud << row_bits) | idx(tau), value (ref(sigma) << 4) | position of the
+  // vertex tau has beyond sigma, where ref(sigma) is sigma's vertices packed
+  // vbits apiece (vertex l at bit l * vbits) when vbits > 0, else its index;
+  // null when col_bits > 60 (the index does not fit beside the position)
   uint64_t* amap;
   uint64_t amap_mask;
+  int vbits;
   // the same map of dimension d - 1 (keys (cloud << col_bits) | idx(sigma)), or null
   const uint64_t* pmap;
   uint64_t pmap_mask;
