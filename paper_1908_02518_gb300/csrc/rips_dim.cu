@@ -1821,11 +1821,15 @@ __device__ __forceinline__ uint32_t lower_bound_u64(const uint64_t* k, uint32_t 
   return lo;
 }
 
+constexpr uint32_t BLOCK_T = WARPS_PER_BLOCK * 32;                // threads of a reduction block
+constexpr int CHUNK_PER = (int)((MID_MERGE + BLOCK_T - 1) / BLOCK_T);  // staged entries per thread
+
 // Merge the ranges [lo[r], hi[r]) of the request's runs (at most MID_MERGE
 // entries together) and append the nonzero sums to (fk, fc) from position
 // `out`; returns how many were appended (the same in every thread).  The ranges
 // are staged in shared memory as consecutive segments with scaled
-// coefficients, then merged two segments at a time, ceil(log2 n) rounds
+// coefficients (every thread issues all its loads before it stores any), then
+// merged two segments at a time, ceil(log2 n) rounds
 // between two buffers: every thread emits a fixed share of a round's output,
 // starting where a merge-path search on its first output puts it (equal keys:
 // the earlier segment first).  In the merged order the entries of one key are
@@ -1839,23 +1843,52 @@ __device__ uint32_t chunk_merge(MergeReq& q, unsigned char* raw, const uint32_t*
   uint64_t* dk = sk + MID_MERGE;
   uint32_t* sc = (uint32_t*)(raw + (size_t)MID_MERGE * 16);
   uint32_t* dc = sc + MID_MERGE;
-  if (tid == 0) {
-    uint32_t acc = 0;
-    for (uint32_t i = 0; i < n; ++i) {
-      q.roff[i] = acc;
-      acc += hi[i] - lo[i];
+  if (wid == 0) {  // segment offsets: a scan over the n <= 32 range lengths
+    const uint32_t len = lane < n ? hi[lane] - lo[lane] : 0u;
+    uint32_t incl = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= (uint32_t)o) incl += t;
     }
-    q.roff[n] = acc;
+    if (lane == 0) q.roff[0] = 0;
+    if (lane < n) q.roff[lane + 1] = incl;
   }
   __syncthreads();
   const uint32_t total = q.roff[n];
-  for (uint32_t e = tid; e < total; e += blockDim.x) {
-    uint32_t r = 0;
-    while (e >= q.roff[r + 1]) ++r;
-    const RunDesc& R = q.d[r];
-    const uint32_t i = lo[r] + e - q.roff[r];
-    sk[e] = R.key[i];
-    sc[e] = R.scale == 1 ? R.coef[i] : (R.coef[i] * R.scale) % p;
+  {  // the segment of each entry by a binary search over the offsets; every load before any store
+    uint32_t seg[CHUNK_PER];
+    uint64_t x[CHUNK_PER];
+    uint32_t cf[CHUNK_PER];
+#pragma unroll
+    for (int k = 0; k < CHUNK_PER; ++k) {
+      const uint32_t e = tid + (uint32_t)k * BLOCK_T;
+      seg[k] = 0;
+      x[k] = 0;
+      cf[k] = 1u;
+      if (e < total) {
+        uint32_t a = 0, b = n;  // roff[a] <= e < roff[b]
+        while (b - a > 1) {
+          const uint32_t m = (a + b) >> 1;
+          if (q.roff[m] <= e) a = m;
+          else b = m;
+        }
+        seg[k] = a;
+        const RunDesc& R = q.d[a];
+        const uint32_t i = lo[a] + e - q.roff[a];
+        x[k] = R.key[i];
+        if (p != 2) cf[k] = R.coef[i];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < CHUNK_PER; ++k) {
+      const uint32_t e = tid + (uint32_t)k * BLOCK_T;
+      if (e < total) {
+        const uint32_t scale = q.d[seg[k]].scale;
+        sk[e] = x[k];
+        sc[e] = (p == 2 || scale == 1) ? cf[k] : (cf[k] * scale) % p;
+      }
+    }
   }
   __syncthreads();
   const uint32_t per = (total + blockDim.x - 1) / blockDim.x;
@@ -1889,10 +1922,11 @@ __device__ uint32_t chunk_merge(MergeReq& q, unsigned char* raw, const uint32_t*
       }
     }
     __syncthreads();
-    if (tid == 0) {  // the merged pairs are the next round's segments
-      uint32_t m = 0;
-      for (uint32_t s2 = 0; s2 < nseg; s2 += 2) q.roff[m++] = q.roff[s2];
-      q.roff[m] = total;
+    if (wid == 0) {  // the merged pairs are the next round's segments (at most 16 + 1 offsets)
+      const uint32_t m = (nseg + 1) / 2;
+      const uint32_t v = lane < m ? q.roff[2 * lane] : total;
+      __syncwarp();
+      if (lane <= m) q.roff[lane] = v;
     }
     uint64_t* tk = sk;
     sk = dk;
@@ -1944,9 +1978,12 @@ constexpr uint32_t MERGE_CHUNKS = 4096;  // most chunks of one big merge
 // chunks of at most MID_MERGE entries: splitters taken every S entries of the
 // longest run cut every run into consecutive ranges (one round of binary
 // searches, in parallel), and chunk_merge merges the ranges chunk after chunk
-// onto the end of the output.  Returns 0 (in every thread) when the arena is
-// full, -1 when the runs are too unevenly spread for chunks of that size (the
-// caller then merges two runs at a time), 1 on success.
+// onto the end of the output.  S is sized so that a chunk holds about 3/4 of
+// MID_MERGE entries when the runs' keys are spread alike; when a chunk comes
+// out too large S is halved (twice at most).  The next chunk's ranges are read
+// while the current one is merged.  Returns 0 (in every thread) when the arena
+// is full, -1 when the runs are too unevenly spread for chunks of that size
+// (the caller then merges two runs at a time), 1 on success.
 __device__ int block_merge_chunked(const RedState& s, unsigned char* raw, MergeReq& q, uint32_t p, uint32_t total) {
   const uint32_t tid = threadIdx.x;
   const uint32_t n = q.n;
@@ -1954,46 +1991,60 @@ __device__ int block_merge_chunked(const RedState& s, unsigned char* raw, MergeR
   for (uint32_t i = 1; i < n; ++i)
     if (q.d[i].len > q.d[L].len) L = i;
   const uint32_t lenL = q.d[L].len;
-  // S entries of the longest run per chunk, so a chunk holds about n * S when the runs are alike
-  uint32_t S = MID_MERGE / (2 * n);
+  uint32_t S = (uint32_t)((unsigned long long)(MID_MERGE * 3 / 4) * lenL / (total ? total : 1));
   if (S < 16) S = 16;
-  uint32_t K = total <= MID_MERGE ? 1u : (lenL + S - 1) / S;
-  if (K < 1) K = 1;
-  if (K > MERGE_CHUNKS) return -1;
-  // arena: the output and the chunk boundaries
-  const unsigned long long want = (unsigned long long)total + (unsigned long long)K * n;
+  const uint32_t Kmax = total <= MID_MERGE ? 1u : (lenL + (S >> 2) - 1) / (S >> 2 ? S >> 2 : 1u);
+  if (Kmax > 4 * MERGE_CHUNKS) return -1;
+  // arena: the output and the chunk boundaries (room for the smallest S tried)
+  const unsigned long long want = (unsigned long long)total + (unsigned long long)Kmax * n;
   if (tid == 0) block_reserve(s, q, want);
   __syncthreads();
   const unsigned long long off = q.off;
   if (off + want > s.r_cap) return 0;
   // bnd[c * n + r] = where run r enters chunk c + 1
   uint32_t* bnd = s.r_coef + off + total;
-  for (uint32_t t = tid; t < (K - 1) * n; t += blockDim.x) {
-    const uint32_t c = t / n, r = t % n;
-    const uint64_t sp = q.d[L].key[(c + 1) * S];
-    bnd[t] = r == L ? (c + 1) * S : lower_bound_u64(q.d[r].key, q.d[r].len, sp);
-  }
   __shared__ int fits;
-  if (tid == 0) fits = 1;
-  __syncthreads();
-  for (uint32_t c = tid; c < K; c += blockDim.x) {
-    uint32_t sz = 0;
-    for (uint32_t r = 0; r < n; ++r) {
-      const uint32_t a0 = c ? bnd[(c - 1) * n + r] : 0u, a1 = c + 1 < K ? bnd[c * n + r] : q.d[r].len;
-      sz += a1 - a0;
+  uint32_t K = 1;
+  for (int attempt = 0; attempt < 3; ++attempt, S >>= 1) {
+    K = total <= MID_MERGE ? 1u : (lenL + S - 1) / S;
+    if (K > MERGE_CHUNKS) return -1;
+    for (uint32_t t = tid; t < (K - 1) * n; t += blockDim.x) {
+      const uint32_t c = t / n, r = t % n;
+      const uint64_t sp = q.d[L].key[(c + 1) * S];
+      bnd[t] = r == L ? (c + 1) * S : lower_bound_u64(q.d[r].key, q.d[r].len, sp);
     }
-    if (sz > MID_MERGE) fits = 0;
+    if (tid == 0) fits = 1;
+    __syncthreads();
+    for (uint32_t c = tid; c < K; c += blockDim.x) {
+      uint32_t sz = 0;
+      for (uint32_t r = 0; r < n; ++r) {
+        const uint32_t a0 = c ? bnd[(c - 1) * n + r] : 0u, a1 = c + 1 < K ? bnd[c * n + r] : q.d[r].len;
+        sz += a1 - a0;
+      }
+      if (sz > MID_MERGE) fits = 0;
+    }
+    __syncthreads();
+    if (fits || K == 1) break;
+    __syncthreads();  // fits is reset by the next attempt
   }
-  __syncthreads();
   if (!fits) return -1;
   uint64_t* fk = s.r_key + off;
   uint32_t* fc = s.r_coef + off;
   __shared__ uint32_t clo[32], chi[32];
   uint32_t out = 0;
+  uint32_t nlo = 0, nhi = 0;  // thread r < n: run r's range in the next chunk
+  if (tid < n) {
+    nlo = 0;
+    nhi = K > 1 ? bnd[tid] : q.d[tid].len;
+  }
   for (uint32_t c = 0; c < K; ++c) {
     if (tid < n) {
-      clo[tid] = c ? bnd[(c - 1) * n + tid] : 0u;
-      chi[tid] = c + 1 < K ? bnd[c * n + tid] : q.d[tid].len;
+      clo[tid] = nlo;
+      chi[tid] = nhi;
+      if (c + 1 < K) {  // read ahead
+        nlo = nhi;
+        nhi = c + 2 < K ? bnd[(c + 1) * n + tid] : q.d[tid].len;
+      }
     }
     __syncthreads();
     out += chunk_merge(q, raw, clo, chi, n, p, fk, fc, out);
