@@ -890,6 +890,17 @@ __device__ __forceinline__ uint32_t scaled(uint32_t c, uint32_t scale, uint32_t 
   return p == 2 ? 1u : (c * scale) % p;
 }
 
+// Remainders mod p of 32-bit numbers by multiplication (Lemire, Kaser and
+// Kurz, "Faster remainder by direct computation", 2019): with
+// M = floor((2^64 - 1) / p) + 1, a mod p = high 64 bits of (M * a mod 2^64) * p,
+// exact for every 32-bit a and p.
+struct ModP {
+  uint32_t p;
+  uint64_t M;
+  __device__ __forceinline__ explicit ModP(uint32_t pp) : p(pp), M(~0ull / pp + 1) {}
+  __device__ __forceinline__ uint32_t operator()(uint32_t x) const { return (uint32_t)__umul64hi(M * x, p); }
+};
+
 // head and look-ahead from the cursor on
 __device__ __forceinline__ void run_head(Run& r, uint32_t p) {
   r.hk = r.cur < r.len ? r.key[r.cur] : ~0ull;
@@ -1839,6 +1850,7 @@ constexpr int CHUNK_PER = (int)((MID_MERGE + BLOCK_T - 1) / BLOCK_T);  // staged
 __device__ uint32_t chunk_merge(MergeReq& q, unsigned char* raw, const uint32_t* lo, const uint32_t* hi, uint32_t n,
                                 uint32_t p, uint64_t* fk, uint32_t* fc, uint32_t out) {
   const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const ModP mod(p);
   uint64_t* sk = (uint64_t*)raw;
   uint64_t* dk = sk + MID_MERGE;
   uint32_t* sc = (uint32_t*)(raw + (size_t)MID_MERGE * 16);
@@ -1886,7 +1898,7 @@ __device__ uint32_t chunk_merge(MergeReq& q, unsigned char* raw, const uint32_t*
       if (e < total) {
         const uint32_t scale = q.d[seg[k]].scale;
         sk[e] = x[k];
-        sc[e] = (p == 2 || scale == 1) ? cf[k] : (cf[k] * scale) % p;
+        sc[e] = (p == 2 || scale == 1) ? cf[k] : mod(cf[k] * scale);
       }
     }
   }
@@ -1936,13 +1948,21 @@ __device__ uint32_t chunk_merge(MergeReq& q, unsigned char* raw, const uint32_t*
     dc = tc;
     __syncthreads();
   }
-  // group sums at the first entry of each key, then pack the nonzero ones
+  // group sums at the first entry of each key (kept in registers: at most
+  // CHUNK_PER entries a thread), then pack the nonzero ones
+  uint32_t gsum[CHUNK_PER];
   uint32_t cnt = 0;
-  for (uint32_t e = e0; e < e1; ++e) {
-    if (e && sk[e - 1] == sk[e]) continue;
-    uint32_t c = sc[e];
-    for (uint32_t x = e + 1; x < total && sk[x] == sk[e]; ++x) c = (c + sc[x]) % p;
-    cnt += c != 0;
+#pragma unroll
+  for (int k = 0; k < CHUNK_PER; ++k) {
+    const uint32_t e = e0 + (uint32_t)k;
+    gsum[k] = 0;
+    if (e < e1 && (e == 0 || sk[e - 1] != sk[e])) {
+      const uint64_t key = sk[e];
+      uint32_t c = sc[e];
+      for (uint32_t x = e + 1; x < total && sk[x] == key; ++x) c = p == 2 ? c ^ sc[x] : mod(c + sc[x]);
+      gsum[k] = c;
+      cnt += c != 0;
+    }
   }
   uint32_t incl = cnt;
 #pragma unroll
@@ -1954,17 +1974,16 @@ __device__ uint32_t chunk_merge(MergeReq& q, unsigned char* raw, const uint32_t*
   __syncthreads();
   uint32_t base = 0, kept = 0;
   for (uint32_t w = 0; w < WARPS_PER_BLOCK; ++w) {
-    if (w < wid) base += q.wsum[w];
-    kept += q.wsum[w];
+    const uint32_t t = q.wsum[w];
+    if (w < wid) base += t;
+    kept += t;
   }
   uint32_t o = out + base + incl - cnt;
-  for (uint32_t e = e0; e < e1; ++e) {
-    if (e && sk[e - 1] == sk[e]) continue;
-    uint32_t c = sc[e];
-    for (uint32_t x = e + 1; x < total && sk[x] == sk[e]; ++x) c = (c + sc[x]) % p;
-    if (c) {
-      fk[o] = sk[e];
-      fc[o] = c;
+#pragma unroll
+  for (int k = 0; k < CHUNK_PER; ++k) {
+    if (gsum[k]) {
+      fk[o] = sk[e0 + (uint32_t)k];
+      fc[o] = gsum[k];
       ++o;
     }
   }
@@ -2188,6 +2207,7 @@ template <bool Z2>
 __device__ __forceinline__ uint64_t ring_pivot(const Rings& R, RingRun& rs, int lane, uint32_t p,
                                                 uint32_t* coef_out) {
   RingRun r = rs;  // the search works on registers; the chain's copy may live in local memory
+  const ModP mod(Z2 ? 2u : p);
   uint64_t m = warp_min_u64(r.hk);
   for (;;) {
     if (m == ~0ull) {
@@ -2210,7 +2230,7 @@ __device__ __forceinline__ uint64_t ring_pivot(const Rings& R, RingRun& rs, int 
     if (Z2) {
       cs = sum & 1u;
     } else {
-      cs = (sum & 0xFFFFFFu) % p;  // at most 32 (p - 1) < 2^21
+      cs = mod(sum & 0xFFFFFFu);  // at most 32 (p - 1) < 2^21
     }
     if (cs) {
       rs = r;
@@ -2226,7 +2246,7 @@ __device__ __forceinline__ uint64_t ring_pivot(const Rings& R, RingRun& rs, int 
       r.hk = hk2;
       r.nk = nk2;
       r.hc = r.nc;
-      r.nc = more ? scaled(R.c[x], r.scale, p) : 0u;
+      r.nc = more ? mod(R.c[x] * r.scale) : 0u;
     }
     if (sum >> (Z2 ? 16 : 24)) {  // refill the rings that ran dry (the head stays; the entry after it is reloaded)
       unsigned need = __ballot_sync(0xffffffffu, refill);
