@@ -1484,6 +1484,10 @@ struct MergeReq {
   uint32_t take;  // the heavy column this block takes next
   // arena slots reserved by this block for generated coboundaries and not yet used
   unsigned long long chunk_off, chunk_left;
+  // the simplex whose coboundary the block generates, set up by warp 0
+  int gv[MAX_DIM + 2];
+  CofacetSums gcs;
+  uint32_t gbeg, gend;
 };
 
 // Block mode takes arena slots (for generated coboundaries and merges) from a
@@ -1541,12 +1545,46 @@ __device__ bool block_gen_sorted(const DimArgs& a, const RedState& s, const CV& 
                                  RunDesc* out, const uint64_t** sk, const uint32_t** sc) {
   const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int d = a.d;
-  int v[MAX_DIM + 2];
-  simplex_vertices(B, cv.n, idx, packed, a.vbits, d, v);
-  CofacetSums cs;
-  cofacet_sums(B, v, d, cs);
-  const int av = v[min_degree_vertex(cv, v, d + 1)];
-  const uint32_t beg = cv.off[av], end = cv.off[av + 1];
+  // Warp 0 sets the simplex up in shared memory once for the block (no thread
+  // keeps its own copy): lane 0 the vertices, then lane l the two binomials
+  // of vertex l that the running sums of the cofacet indices add up (a scan
+  // each) and the length of its neighbour list (the shortest is scanned).
+  if (wid == 0) {
+    if (lane == 0) simplex_vertices(B, cv.n, idx, packed, a.vbits, d, q.gv);
+    __syncwarp();
+    const bool mine = lane <= (uint32_t)d;
+    const int vl = mine ? q.gv[lane] : 0;
+    const uint64_t up = mine ? B(vl, d + 2 - (int)lane) : 0ull;  // joins above[c] for c > lane
+    const uint64_t dn = mine ? B(vl, d + 1 - (int)lane) : 0ull;  // joins below[c] for c <= lane
+    const uint32_t o0 = mine ? cv.off[vl] : 0u, o1 = mine ? cv.off[vl + 1] : 0u;
+    uint64_t iu = up, idn = dn;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t tu = __shfl_up_sync(0xffffffffu, iu, o);
+      const uint64_t td = __shfl_up_sync(0xffffffffu, idn, o);
+      if (lane >= (uint32_t)o) {
+        iu += tu;
+        idn += td;
+      }
+    }
+    const uint64_t dn_all = __shfl_sync(0xffffffffu, idn, 31);
+    if (lane <= (uint32_t)d + 1) {
+      q.gcs.above[lane] = iu - up;
+      q.gcs.below[lane] = dn_all - (idn - dn);
+    }
+    const uint32_t dg = mine ? o1 - o0 : 0xFFFFFFFFu;
+    const uint32_t mdg = __reduce_min_sync(0xffffffffu, dg);
+    const int best = __ffs(__ballot_sync(0xffffffffu, mine && dg == mdg)) - 1;
+    const uint32_t b0 = __shfl_sync(0xffffffffu, o0, best), b1 = __shfl_sync(0xffffffffu, o1, best);
+    if (lane == 0) {
+      q.gbeg = b0;
+      q.gend = b1;
+    }
+  }
+  __syncthreads();
+  const int* v = q.gv;
+  const CofacetSums& cs = q.gcs;
+  const uint32_t beg = q.gbeg, end = q.gend;
   const uint32_t deg = end - beg;  // at most this many cofacets
   uint32_t p2 = 1;
   while (p2 < deg) p2 <<= 1;
