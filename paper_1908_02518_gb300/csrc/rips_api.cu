@@ -673,7 +673,7 @@ int run_batch(Workspace& w, const float* dD, const std::vector<int64_t>& ns, int
     CR(ensure(w.claim, (size_t)(M + 1) * 4));
     CR(ensure(w.reduce, (size_t)(M + 1) * 4));
     CR(ensure(w.heavy, (size_t)(M + 1) * 8));
-    CR(ensure(w.lists, 128));
+    CR(ensure(w.lists, LISTS_BYTES));
     CR(ensure(w.r_top, 16));
     // a generated coboundary holds at most max_deg entries (sorted in a power-of-two buffer)
     const int blocks = M ? reduction_blocks(a, M) : 1;
@@ -703,7 +703,7 @@ int run_batch(Workspace& w, const float* dD, const std::vector<int64_t>& ns, int
       w.r_cap = rcap;
       CK(cudaMemsetAsync(w.tkeys[tb].p, 0xFF, (size_t)tcap * 8, s));
       CK(cudaMemsetAsync(w.tvals[tb].p, 0xFF, (size_t)tcap * 4, s));
-      CK(cudaMemsetAsync(w.lists.p, 0, 128, s));
+      CK(cudaMemsetAsync(w.lists.p, 0, LISTS_BYTES, s));
       CK(cudaMemsetAsync(w.r_top.p, 0, 16, s));
       uint32_t* counts = P<uint32_t>(w.lists);
       RedState rs;
@@ -731,6 +731,8 @@ int run_batch(Workspace& w, const float* dD, const std::vector<int64_t>& ns, int
       rs.max_chain = counts + 7;
       rs.heartbeat = counts + 12;
       rs.added = P<unsigned long long>(w.lists) + 7;
+      rs.help = (HelpBoard*)(P<unsigned char>(w.lists) + 256);
+      rs.idle = counts + 4;
       rs.barrier_ns = lim.barrier_wait_ns ? lim.barrier_wait_ns : 30ull * 1000 * 1000 * 1000;
       rs.chain_ns = lim.chain_ns ? lim.chain_ns : 600ull * 1000 * 1000 * 1000;
       rs.err = P<uint32_t>(w.err);
@@ -1252,7 +1254,7 @@ int plan_create(PlanState& pl, const int64_t* offsets, int32_t batch, int32_t k,
   CR(ensure(w.claim, (E + 1) * 4));
   CR(ensure(w.reduce, (E + 1) * 4));
   CR(ensure(w.heavy, (E + 1) * 8));
-  CR(ensure(w.lists, 128));
+  CR(ensure(w.lists, LISTS_BYTES));
   CR(ensure(w.r_top, 16));
   CR(ensure(w.r_key, pl.arena * 8));
   CR(ensure(w.r_coef, pl.arena * 4));
@@ -1341,7 +1343,7 @@ int plan_run(PlanState& pl, const float* d_points, cudaStream_t s) {
                     pl.cb + a.rank_bits + a.col_bits, w.sorttmp.p, w.sorttmp.cap, &calt, s));
   CK(cudaMemsetAsync(w.tkeys[0].p, 0xFF, (size_t)pl.tcap * 8, s));
   CK(cudaMemsetAsync(w.tvals[0].p, 0xFF, (size_t)pl.tcap * 4, s));
-  CK(cudaMemsetAsync(w.lists.p, 0, 128, s));
+  CK(cudaMemsetAsync(w.lists.p, 0, LISTS_BYTES, s));
   CK(cudaMemsetAsync(w.r_top.p, 0, 16, s));
   uint32_t* counts = P<uint32_t>(w.lists);
   RedState rs;
@@ -1369,6 +1371,8 @@ int plan_run(PlanState& pl, const float* d_points, cudaStream_t s) {
   rs.max_chain = counts + 7;
   rs.heartbeat = counts + 12;
   rs.added = P<unsigned long long>(w.lists) + 7;
+  rs.help = (HelpBoard*)(P<unsigned char>(w.lists) + 256);
+  rs.idle = counts + 4;
   const rips_limits_t lim = current_limits();
   rs.barrier_ns = lim.barrier_wait_ns ? lim.barrier_wait_ns : 30ull * 1000 * 1000 * 1000;
   rs.chain_ns = lim.chain_ns ? lim.chain_ns : 600ull * 1000 * 1000 * 1000;

@@ -1490,6 +1490,44 @@ struct MergeReq {
   uint32_t gbeg, gend;
 };
 
+}  // namespace
+
+// A large run merge shared out (block_merge_helped): the block that owns it
+// opens a job in a free slot of the help board, and blocks waiting at the grid
+// barrier claim its chunks, first to merge them (phase 1), then to copy their
+// merged entries into place (phase 2).  A claim packs the job with the chunk,
+// so a claim that succeeds pins the job: it cannot close before that chunk is
+// done.  The fields every waiting block polls, the claim counters and the
+// completion counters sit in separate cache lines.
+constexpr int HELP_SLOTS = 8;
+struct alignas(128) HelpSlot {
+  unsigned job;              // the open job, 0 when none
+  unsigned phase;            // 1 merging, 2 copying out
+  unsigned K, n, p;
+  const uint32_t* bnd;       // chunk boundaries, (K - 1) x n (see block_merge_chunked)
+  uint64_t* tk;              // merged chunks, chunk c from inoff[c]
+  uint32_t* tc;
+  uint64_t* fk;              // the merged run
+  uint32_t* fc;
+  uint32_t* inoff;           // per chunk: where its input, and its merged entries, start
+  uint32_t* kept;            // per chunk: entries kept
+  uint32_t* outoff;          // per chunk: where its entries go in the merged run
+  alignas(128) unsigned long long next;  // (job << 32) | next chunk to merge
+  unsigned long long next2;              // (job << 32) | next chunk to copy out
+  alignas(128) unsigned done;            // chunks merged
+  unsigned done2;                        // chunks copied out
+  alignas(128) unsigned lock;            // owning block + 1, 0 when free
+  unsigned jobs;                         // jobs opened in this slot so far
+  RunDesc d[32];                         // the runs
+};
+struct HelpBoard {
+  alignas(128) unsigned active;  // bit i: slot i has an open job
+  HelpSlot slot[HELP_SLOTS];
+};
+static_assert(256 + sizeof(HelpBoard) <= LISTS_BYTES, "the help board fits the control block");
+
+namespace {
+
 // Block mode takes arena slots (for generated coboundaries and merges) from a
 // block-local chunk of at least GEN_CHUNK entries, so most requests make no
 // global atomic.  Called by one thread; the slots start at q.off.  Whether they
@@ -1926,8 +1964,8 @@ __device__ uint32_t chunk_merge(MergeReq& q, unsigned char* raw, const uint32_t*
         seg[k] = a;
         const RunDesc& R = q.d[a];
         const uint32_t i = lo[a] + e - q.roff[a];
-        x[k] = R.key[i];
-        if (p != 2) cf[k] = R.coef[i];
+        x[k] = __ldcg(R.key + i);  // through L2: runs may come from other blocks
+        if (p != 2) cf[k] = __ldcg(R.coef + i);
       }
     }
 #pragma unroll
@@ -2029,6 +2067,276 @@ __device__ uint32_t chunk_merge(MergeReq& q, unsigned char* raw, const uint32_t*
   return kept;
 }
 
+// ---------------------------------------------------------------- shared-out merges
+constexpr uint32_t HELP_MIN_CHUNKS = 4;  // a merge of fewer chunks stays in its block
+constexpr unsigned HELP_MIN_IDLE = 8;    // blocks waiting at the grid barrier before a merge is shared out
+
+// Thread 0: claims a chunk of the slot's open job on the counter of its
+// current phase; returns it (and the job and phase) or -1.  The chunk may lie
+// past the job's last one (the bound read before the claim is not pinned yet):
+// callers check it against the job's chunk count read after the claim.
+__device__ int help_claim_slot(HelpSlot* hb, unsigned* job, unsigned* phase) {
+  const unsigned jb = *(volatile unsigned*)&hb->job;
+  if (!jb) return -1;
+  __threadfence();
+  const unsigned ph = *(volatile unsigned*)&hb->phase;
+  const unsigned K = *(volatile unsigned*)&hb->K;
+  unsigned long long* ctr = ph == 2 ? &hb->next2 : &hb->next;
+  unsigned long long old = *(volatile unsigned long long*)ctr;
+  for (int t = 0; t < 64; ++t) {
+    if ((unsigned)(old >> 32) != jb || (unsigned)old >= K) return -1;
+    const unsigned long long got = atomicCAS(ctr, old, old + 1);
+    if (got == old) {
+      *job = jb;
+      *phase = ph;
+      __threadfence();
+      return (int)(unsigned)old;
+    }
+    old = got;
+  }
+  return -1;
+}
+
+// Thread 0 of a waiting block: a chunk of any open job (slots tried from one
+// that depends on the block, so waiting blocks spread over the jobs).
+__device__ int help_claim(HelpBoard* B, int* slot, unsigned* phase) {
+  const unsigned act = *(volatile unsigned*)&B->active;
+  if (!act) return -1;
+  for (int k = 0; k < HELP_SLOTS; ++k) {
+    const int i = (int)((blockIdx.x + (unsigned)k) % HELP_SLOTS);
+    if (!((act >> i) & 1u)) continue;
+    unsigned jb = 0;
+    const int c = help_claim_slot(&B->slot[i], &jb, phase);
+    if (c >= 0) {
+      *slot = i;
+      return c;
+    }
+  }
+  return -1;
+}
+
+// The job's fields, as thread 0 reads them once its claim pins the job
+struct HelpView {
+  uint32_t K, n, p;
+  const uint32_t* bnd;
+  uint64_t* tk;
+  uint32_t* tc;
+  uint64_t* fk;
+  uint32_t* fc;
+  uint32_t* inoff;
+  uint32_t* kept;
+  uint32_t* outoff;
+  uint32_t in;  // the chunk's inoff
+};
+
+// The whole block: chunk c of the job (claimed by thread 0 for `phase`):
+// phase 1 merges it into the job's chunk area and records its entries kept,
+// phase 2 copies its merged entries to their place in the merged run.  The
+// block's own request (q.d) takes the job's runs.
+__device__ void help_chunk(HelpSlot* hb, unsigned char* raw, MergeReq& q, int c, unsigned phase) {
+  const uint32_t tid = threadIdx.x, lane = tid & 31;
+  __shared__ HelpView v;
+  __shared__ uint32_t hlo[32], hhi[32];
+  __shared__ int valid;
+  if (tid == 0) {
+    volatile HelpSlot* b = hb;
+    v.K = b->K;
+    v.n = b->n;
+    v.p = b->p;
+    v.bnd = b->bnd;
+    v.tk = b->tk;
+    v.tc = b->tc;
+    v.fk = b->fk;
+    v.fc = b->fc;
+    v.inoff = b->inoff;
+    v.kept = b->kept;
+    v.outoff = b->outoff;
+    valid = (uint32_t)c < v.K;
+  }
+  __syncthreads();
+  if (!valid) {
+    __syncthreads();  // v and valid are reused by the next claim
+    return;
+  }
+  const uint32_t n = v.n, K = v.K, uc = (uint32_t)c;
+  if (phase == 1) {
+    if (tid < n) {
+      volatile const RunDesc* src = hb->d + tid;
+      q.d[tid] = RunDesc{src->key, src->coef, src->len, src->scale};
+    }
+    __syncthreads();
+    if (tid < 32) {
+      const uint32_t lo = tid < n && uc ? __ldcg(v.bnd + (size_t)(uc - 1) * n + tid) : 0u;
+      const uint32_t hi = tid < n ? (uc + 1 < K ? __ldcg(v.bnd + (size_t)uc * n + tid) : q.d[tid].len) : 0u;
+      if (tid < n) {
+        hlo[tid] = lo;
+        hhi[tid] = hi;
+      }
+      const uint32_t in = __reduce_add_sync(0xffffffffu, lo);
+      if (lane == 0) v.in = in;
+    }
+    __syncthreads();
+    const uint32_t kept = chunk_merge(q, raw, hlo, hhi, n, v.p, v.tk + v.in, v.tc + v.in, 0);
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+      v.inoff[uc] = v.in;
+      v.kept[uc] = kept;
+      __threadfence();
+      atomicAdd(&hb->done, 1u);
+    }
+  } else {
+    const uint32_t cnt = __ldcg(v.kept + uc), src = __ldcg(v.inoff + uc), dst = __ldcg(v.outoff + uc);
+    for (uint32_t i = tid; i < cnt; i += blockDim.x) {
+      v.fk[dst + i] = __ldcg(v.tk + src + i);
+      v.fc[dst + i] = __ldcg(v.tc + src + i);
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) atomicAdd(&hb->done2, 1u);
+  }
+  __syncthreads();  // v, hlo, hhi and valid are reused by the next claim
+}
+
+// Thread 0: waits (bounded by limit_ns) until *ctr reaches K; false on timeout.
+__device__ bool help_wait(const unsigned* ctr, unsigned K, unsigned long long limit_ns) {
+  const unsigned long long t0 = global_ns();
+  while (*(volatile const unsigned*)ctr < K) {
+    __nanosleep(64);
+    if (global_ns() - t0 > limit_ns) return false;
+  }
+  __threadfence();
+  return true;
+}
+
+// A merge of K >= HELP_MIN_CHUNKS chunks (boundaries bnd, output fk/fc) shared
+// out through the help board while blocks wait at the grid barrier; this block
+// takes chunks like any helper.  Returns 1 when the merged run is in q.d[0], 0
+// when the arena is full, -2 when the board is taken (the caller merges alone).
+// A helper that does not finish within the barrier's wait limit sets
+// ERRF_TIMEOUT and leaves an empty run.
+__device__ int block_merge_helped(const RedState& s, unsigned char* raw, MergeReq& q, uint32_t p, uint32_t total,
+                                  uint32_t K, const uint32_t* bnd, uint64_t* fk, uint32_t* fc) {
+  const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const uint32_t n = q.n;
+  __shared__ int st, slot;
+  __shared__ uint32_t kept_total;
+  if (tid == 0) {  // a free slot
+    st = -2;
+    for (int k = 0; k < HELP_SLOTS && st != 1; ++k) {
+      const int i = (int)((blockIdx.x + (unsigned)k) % HELP_SLOTS);
+      if (atomicCAS(&s.help->slot[i].lock, 0u, blockIdx.x + 1u) == 0u) {
+        st = 1;
+        slot = i;
+      }
+    }
+  }
+  __syncthreads();
+  if (st != 1) return -2;
+  HelpSlot* hb = &s.help->slot[slot];
+  // room for the merged chunks and three per-chunk counts
+  const unsigned long long want = (unsigned long long)total + 3ull * K;
+  if (tid == 0) block_reserve(s, q, want);
+  __syncthreads();
+  const unsigned long long off = q.off;
+  if (off + want > s.r_cap) {
+    __syncthreads();
+    if (tid == 0) atomicExch(&hb->lock, 0u);
+    return 0;
+  }
+  if (tid == 0) {
+    const unsigned job = hb->jobs + 1u;
+    hb->jobs = job;
+    hb->next = (unsigned long long)job << 32;
+    hb->next2 = (unsigned long long)job << 32;
+    hb->done = 0;
+    hb->done2 = 0;
+    __threadfence();  // stale claims on an earlier job fail from here on
+    hb->K = K;
+    hb->n = n;
+    hb->p = p;
+    hb->bnd = bnd;
+    hb->tk = s.r_key + off;
+    hb->tc = s.r_coef + off;
+    hb->fk = fk;
+    hb->fc = fc;
+    hb->inoff = s.r_coef + off + total;
+    hb->kept = hb->inoff + K;
+    hb->outoff = hb->kept + K;
+    hb->phase = 1;
+  }
+  if (tid < n) hb->d[tid] = q.d[tid];
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    atomicExch(&hb->job, (unsigned)(hb->jobs));
+    atomicOr(&s.help->active, 1u << slot);
+  }
+  for (unsigned phase = 1; phase <= 2; ++phase) {
+    __shared__ int hc;
+    for (;;) {
+      if (tid == 0) {
+        unsigned jb = 0, ph = 0;
+        hc = help_claim_slot(hb, &jb, &ph);
+        if (hc >= 0 && ph != phase) hc = -1;  // cannot happen: the phase changes only below
+      }
+      __syncthreads();
+      const int c = hc;
+      __syncthreads();
+      if (c < 0) break;
+      help_chunk(hb, raw, q, c, phase);
+    }
+    if (tid == 0 && st == 1 && !help_wait(phase == 1 ? &hb->done : &hb->done2, K, s.barrier_ns)) st = 0;
+    __syncthreads();
+    if (st != 1) break;
+    if (phase == 1) {  // where each chunk's entries go: a scan of the kept counts
+      uint32_t* kept = s.r_coef + off + total + K;
+      uint32_t* outoff = kept + K;
+      const uint32_t per = (K + blockDim.x - 1) / blockDim.x;
+      const uint32_t c0 = min(tid * per, K), c1 = min(c0 + per, K);
+      uint32_t sum = 0;
+      for (uint32_t c = c0; c < c1; ++c) sum += __ldcg(kept + c);
+      uint32_t incl = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl += t;
+      }
+      if (lane == 31) q.wsum[wid] = incl;
+      __syncthreads();
+      uint32_t base = 0, all = 0;
+      for (uint32_t w = 0; w < WARPS_PER_BLOCK; ++w) {
+        if (w < wid) base += q.wsum[w];
+        all += q.wsum[w];
+      }
+      uint32_t o = base + incl - sum;
+      for (uint32_t c = c0; c < c1; ++c) {
+        outoff[c] = o;
+        o += __ldcg(kept + c);
+      }
+      if (tid == 0) kept_total = all;
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) atomicExch(&hb->phase, 2u);
+    }
+  }
+  if (tid == 0) {
+    if (st == 1) {
+      atomicAnd(&s.help->active, ~(1u << slot));
+      atomicExch(&hb->job, 0u);
+      __threadfence();
+      atomicExch(&hb->lock, 0u);
+      q.d[0] = RunDesc{fk, fc, kept_total, 1};
+      atomicAdd(s.compacted, (unsigned long long)total);
+    } else {  // a helper overran the wait: the dimension fails; the job stays open
+      set_error(s.err, ERRF_TIMEOUT);
+      q.d[0] = RunDesc{fk, fc, 0u, 1};
+    }
+  }
+  __syncthreads();
+  return 1;
+}
+
 constexpr uint32_t MERGE_CHUNKS = 4096;  // most chunks of one big merge
 
 // The request's runs merged in one pass into one run of scale 1 in q.d[0], in
@@ -2087,6 +2395,10 @@ __device__ int block_merge_chunked(const RedState& s, unsigned char* raw, MergeR
   if (!fits) return -1;
   uint64_t* fk = s.r_key + off;
   uint32_t* fc = s.r_coef + off;
+  if (s.help && K >= HELP_MIN_CHUNKS && *(volatile const unsigned*)s.idle >= HELP_MIN_IDLE) {
+    const int r = block_merge_helped(s, raw, q, p, total, K, bnd, fk, fc);
+    if (r != -2) return r;  // else the board is taken: merge here
+  }
   __shared__ uint32_t clo[32], chi[32];
   uint32_t out = 0;
   uint32_t nlo = 0, nhi = 0;  // thread r < n: run r's range in the next chunk
@@ -2564,40 +2876,71 @@ __device__ void reduce_one_block(const DimArgs& a, const RedState& s, const Bino
 // wait is bounded: when limit_ns pass with no block making progress
 // (the heartbeat counter, bumped by long chains of additions, stands still) the
 // block records ERRF_TIMEOUT and returns false, and the caller leaves the
-// kernel.
-__device__ bool grid_barrier(unsigned* count, unsigned* gen, const unsigned* heartbeat, unsigned long long limit_ns,
-                             uint32_t* err) {
-  __shared__ int ok;
+// kernel.  While it waits, a block takes chunks of a merge shared out on the
+// help board (block_merge_helped), with its own request and staging area.
+__device__ bool grid_barrier(unsigned* count, unsigned* gen, const RedState& s, uint32_t* err, unsigned char* raw,
+                             MergeReq& q) {
+  __shared__ int ok, st, hc, hp, hs;
+  enum { WAIT = 0, DONE = 1, HELP = 2 };
+  const unsigned* heartbeat = s.heartbeat;
+  const unsigned long long limit_ns = s.barrier_ns;
   __syncthreads();
+  unsigned g = 0, hb = 0;
+  unsigned long long t0 = 0;
   if (threadIdx.x == 0) {
     ok = 1;
-    const unsigned g = *(volatile unsigned*)gen;
+    st = WAIT;
+    g = *(volatile unsigned*)gen;
     __threadfence();
     if (atomicAdd(count, 1u) == gridDim.x - 1) {
       atomicExch(count, 0u);
       __threadfence();
       atomicAdd(gen, 1u);
+      st = DONE;
     } else {
-      unsigned long long t0 = global_ns();
-      unsigned hb = *(volatile const unsigned*)heartbeat;
-      while (*(volatile unsigned*)gen == g) {
-        __nanosleep(128);
-        const unsigned long long now = global_ns();
-        if (now - t0 > limit_ns) {
-          const unsigned h = *(volatile const unsigned*)heartbeat;
-          if (h != hb) {  // another block is still working
-            hb = h;
-            t0 = now;
-            continue;
+      t0 = global_ns();
+      hb = *(volatile const unsigned*)heartbeat;
+    }
+  }
+  for (;;) {
+    if (threadIdx.x == 0 && st != DONE) {
+      st = WAIT;
+      if (*(volatile unsigned*)gen != g) {
+        st = DONE;
+      } else {
+        unsigned ph = 0;
+        int sl = 0;
+        const int c = s.help ? help_claim(s.help, &sl, &ph) : -1;
+        if (c >= 0) {
+          st = HELP;
+          hc = c;
+          hp = (int)ph;
+          hs = sl;
+          t0 = global_ns();  // helping is progress
+        } else {
+          __nanosleep(128);
+          const unsigned long long now = global_ns();
+          if (now - t0 > limit_ns) {
+            const unsigned h = *(volatile const unsigned*)heartbeat;
+            if (h != hb) {  // another block is still working
+              hb = h;
+              t0 = now;
+            } else {
+              set_error(err, ERRF_TIMEOUT);
+              ok = 0;
+              st = DONE;
+            }
           }
-          set_error(err, ERRF_TIMEOUT);
-          ok = 0;
-          break;
         }
       }
     }
-    __threadfence();
+    __syncthreads();
+    const int now_st = st;
+    if (now_st == DONE) break;
+    if (now_st == HELP) help_chunk(&s.help->slot[hs], raw, q, hc, (unsigned)hp);
+    __syncthreads();
   }
+  if (threadIdx.x == 0) __threadfence();
   __syncthreads();
   return ok != 0;
 }
@@ -2645,7 +2988,7 @@ __global__ void __launch_bounds__(256, 2) reduce_persistent_kernel(DimArgs a, Re
 
   for (uint32_t j = warp_id; j < ncols; j += warps)
     init_column(a, s, B, lane, tile, j, &claim_cnt[0], &heavy_cnt[0], heavy[0]);
-  if (!grid_barrier(bar_count, bar_gen, s.heartbeat, s.barrier_ns, a.err)) return;
+  if (!grid_barrier(bar_count, bar_gen, s, a.err, red_smem, req)) return;
   uint32_t r = 0;
   for (;; ++r) {
     const int src = r & 1, dst = src ^ 1;
@@ -2661,7 +3004,7 @@ __global__ void __launch_bounds__(256, 2) reduce_persistent_kernel(DimArgs a, Re
       *light_next = 0;
       *heavy_next = 0;
     }
-    if (!grid_barrier(bar_count, bar_gen, s.heartbeat, s.barrier_ns, a.err)) return;
+    if (!grid_barrier(bar_count, bar_gen, s, a.err, red_smem, req)) return;
     if (tid == 0) {
       claim_cnt[src] = 0;
       red_cnt[dst] = 0;
@@ -2690,7 +3033,7 @@ __global__ void __launch_bounds__(256, 2) reduce_persistent_kernel(DimArgs a, Re
         reduce_one(a, s, B, lane, tile, s.reduce_list[t], &claim_cnt[dst], &heavy_cnt[dst], heavy[dst]);
       }
     }
-    if (!grid_barrier(bar_count, bar_gen, s.heartbeat, s.barrier_ns, a.err)) return;
+    if (!grid_barrier(bar_count, bar_gen, s, a.err, red_smem, req)) return;
   }
   if (tid == 0) ctl[6] = r;
 }

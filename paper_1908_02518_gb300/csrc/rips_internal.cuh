@@ -207,6 +207,11 @@ struct DimArgs {
   uint32_t opts;                   // RIPS_OPT_* switches (rips_set_options)
 };
 
+struct HelpBoard;  // rips_dim.cu
+// bytes of the reduction's control block: counters and cursors in the first
+// 256, the help board after them (zeroed together before every launch)
+constexpr size_t LISTS_BYTES = 16384;
+
 // Reduction state (device pointers) shared by the reduction kernels
 struct RedState {
   // columns in processing order
@@ -239,6 +244,11 @@ struct RedState {
   uint32_t* max_chain;            // longest chain of additions (profiling)
   unsigned* heartbeat;            // bumped while chains of additions make progress
   unsigned long long* added;      // entries of the columns added (profiling)
+  // board through which a block with a large run merge hands chunks of it to
+  // blocks waiting at the grid barrier (zeroed before the launch; null: none),
+  // and the number of blocks waiting there
+  struct HelpBoard* help;
+  const unsigned* idle;
   unsigned long long barrier_ns;  // grid-barrier wait without progress before giving up
   unsigned long long chain_ns;    // one chain of additions before giving up
   uint32_t* err;
