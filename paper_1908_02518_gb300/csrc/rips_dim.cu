@@ -2337,7 +2337,77 @@ __device__ int block_merge_helped(const RedState& s, unsigned char* raw, MergeRe
   return 1;
 }
 
-constexpr uint32_t MERGE_CHUNKS = 4096;  // most chunks of one big merge
+constexpr uint32_t MERGE_CHUNKS = 1u << 16;  // most chunks of one big merge (75 M entries at 3/4 full)
+
+constexpr uint32_t SAMPLE_CAP = 2048;  // splitter samples sorted in shared memory
+
+// Chunk boundaries from samples of every run, for runs whose keys are spread
+// too unevenly for splitters from the longest one: every run offers the key at
+// every G-th position (G >= total / SAMPLE_CAP), the block sorts the samples,
+// and every m-th one is a splitter.  A run that offers s samples inside a
+// chunk has at most (s + 1) G entries there, and a chunk takes at most m + n - 1
+// samples (its m in sorted order, and up to n - 1 copies of its splitter key
+// sorted before it), so it holds at most (m + 2n - 1) G <= MID_MERGE.  Returns 1 with the chunk count and the boundaries
+// (in fresh arena slots, laid out as block_merge_chunked's), 0 when the arena
+// is full, -1 when no sample gap is small enough.  Called by the whole block.
+__device__ int sample_splitters(const RedState& s, unsigned char* raw, MergeReq& q, uint32_t total, uint32_t* Kout,
+                                uint32_t** bnd_out) {
+  const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const uint32_t n = q.n;
+  uint32_t G = (total + SAMPLE_CAP - 1) / SAMPLE_CAP;
+  if (G < 16) G = 16;
+  if ((2 * n + 1) * G > MID_MERGE) return -1;
+  const uint32_t m = MID_MERGE / G - 2 * n + 1;
+  uint64_t* sk = (uint64_t*)raw;
+  uint32_t* sc = (uint32_t*)(raw + (size_t)SAMPLE_CAP * 8);
+  if (wid == 0) {  // samples per run (positions G, 2G, ... below its length) and their offsets
+    const uint32_t len = lane < n ? q.d[lane].len : 0u;
+    const uint32_t cnt = len ? (len - 1) / G : 0u;
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= (uint32_t)o) incl += t;
+    }
+    if (lane == 0) q.roff[0] = 0;
+    if (lane < n) q.roff[lane + 1] = incl;
+  }
+  __syncthreads();
+  const uint32_t ns = q.roff[n];  // at most total / G <= SAMPLE_CAP
+  uint32_t n2 = 1;
+  while (n2 < ns) n2 <<= 1;
+  for (uint32_t e = tid; e < n2; e += blockDim.x) {
+    uint64_t key = ~0ull;
+    if (e < ns) {
+      uint32_t a = 0, b = n;  // roff[a] <= e < roff[b]
+      while (b - a > 1) {
+        const uint32_t mid = (a + b) >> 1;
+        if (q.roff[mid] <= e) a = mid;
+        else b = mid;
+      }
+      key = __ldcg(q.d[a].key + (size_t)(e - q.roff[a] + 1) * G);
+    }
+    sk[e] = key;
+    sc[e] = 0u;
+  }
+  __syncthreads();
+  block_bitonic(sk, sc, n2);
+  const uint32_t K = ns ? (ns + m - 1) / m : 1u;  // splitters sk[m], sk[2m], ..., sk[(K - 1) m]
+  const unsigned long long want = (unsigned long long)(K - 1) * n + 1;
+  if (tid == 0) block_reserve(s, q, want);
+  __syncthreads();
+  const unsigned long long off = q.off;
+  if (off + want > s.r_cap) return 0;
+  uint32_t* bnd = s.r_coef + off;
+  for (uint32_t t = tid; t < (K - 1) * n; t += blockDim.x) {
+    const uint32_t c = t / n, r = t % n;
+    bnd[t] = lower_bound_u64(q.d[r].key, q.d[r].len, sk[(c + 1) * m]);
+  }
+  __syncthreads();
+  *Kout = K;
+  *bnd_out = bnd;
+  return 1;
+}
 
 // The request's runs merged in one pass into one run of scale 1 in q.d[0], in
 // chunks of at most MID_MERGE entries: splitters taken every S entries of the
@@ -2345,7 +2415,8 @@ constexpr uint32_t MERGE_CHUNKS = 4096;  // most chunks of one big merge
 // searches, in parallel), and chunk_merge merges the ranges chunk after chunk
 // onto the end of the output.  S is sized so that a chunk holds about 3/4 of
 // MID_MERGE entries when the runs' keys are spread alike; when a chunk comes
-// out too large S is halved (twice at most).  The next chunk's ranges are read
+// out too large S is halved (twice at most), and then splitters come from
+// samples of every run (sample_splitters).  The next chunk's ranges are read
 // while the current one is merged.  Returns 0 (in every thread) when the arena
 // is full, -1 when the runs are too unevenly spread for chunks of that size
 // (the caller then merges two runs at a time), 1 on success.
@@ -2392,7 +2463,10 @@ __device__ int block_merge_chunked(const RedState& s, unsigned char* raw, MergeR
     if (fits || K == 1) break;
     __syncthreads();  // fits is reset by the next attempt
   }
-  if (!fits) return -1;
+  if (!fits) {  // splitters from samples of every run
+    const int r = sample_splitters(s, raw, q, total, &K, &bnd);
+    if (r != 1) return r;
+  }
   uint64_t* fk = s.r_key + off;
   uint32_t* fc = s.r_coef + off;
   if (s.help && K >= HELP_MIN_CHUNKS && *(volatile const unsigned*)s.idle >= HELP_MIN_IDLE) {
