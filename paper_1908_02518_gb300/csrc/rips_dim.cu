@@ -2429,7 +2429,9 @@ __device__ int block_merge_chunked(const RedState& s, unsigned char* raw, MergeR
   const uint32_t lenL = q.d[L].len;
   uint32_t S = (uint32_t)((unsigned long long)(MID_MERGE * 3 / 4) * lenL / (total ? total : 1));
   if (S < 16) S = 16;
-  const uint32_t Kmax = total <= MID_MERGE ? 1u : (lenL + (S >> 2) - 1) / (S >> 2 ? S >> 2 : 1u);
+  constexpr uint32_t T2 = MID_MERGE * 3 / 4;  // entries of a two-run chunk
+  uint32_t Kmax = total <= MID_MERGE ? 1u : (lenL + (S >> 2) - 1) / (S >> 2 ? S >> 2 : 1u);
+  if (n == 2) Kmax = max(Kmax, (total + T2 - 1) / T2);
   if (Kmax > 4 * MERGE_CHUNKS) return -1;
   // arena: the output and the chunk boundaries (room for the smallest S tried)
   const unsigned long long want = (unsigned long long)total + (unsigned long long)Kmax * n;
@@ -2441,7 +2443,30 @@ __device__ int block_merge_chunked(const RedState& s, unsigned char* raw, MergeR
   uint32_t* bnd = s.r_coef + off + total;
   __shared__ int fits;
   uint32_t K = 1;
-  for (int attempt = 0; attempt < 3; ++attempt, S >>= 1) {
+  if (n == 2 && total > MID_MERGE) {
+    // two runs: splitters at merge-path diagonals, every T2 merged entries (the
+    // key there, looked up in both runs, keeps equal keys together), so every
+    // chunk holds T2 entries, give or take one
+    K = (total + T2 - 1) / T2;
+    if (K > MERGE_CHUNKS) return -1;
+    const RunDesc A = q.d[0], Bd = q.d[1];
+    for (uint32_t c = tid; c + 1 < K; c += blockDim.x) {
+      const uint32_t dg = (c + 1) * T2;  // below total
+      uint32_t lo = dg > Bd.len ? dg - Bd.len : 0u, hi = min(dg, A.len);
+      while (lo < hi) {  // A entries among the first dg merged ones (equal keys: A first)
+        const uint32_t mid = (lo + hi) >> 1;
+        if (A.key[mid] <= Bd.key[dg - mid - 1]) lo = mid + 1;
+        else hi = mid;
+      }
+      const uint32_t i = lo, j = dg - lo;
+      const uint64_t x = j >= Bd.len ? A.key[i] : (i >= A.len ? Bd.key[j] : min(A.key[i], Bd.key[j]));
+      bnd[c * 2] = lower_bound_u64(A.key, A.len, x);
+      bnd[c * 2 + 1] = lower_bound_u64(Bd.key, Bd.len, x);
+    }
+    if (tid == 0) fits = 1;
+    __syncthreads();
+  }
+  for (int attempt = 0; attempt < 3 && !(n == 2 && total > MID_MERGE); ++attempt, S >>= 1) {
     K = total <= MID_MERGE ? 1u : (lenL + S - 1) / S;
     if (K > MERGE_CHUNKS) return -1;
     for (uint32_t t = tid; t < (K - 1) * n; t += blockDim.x) {
@@ -2510,29 +2535,52 @@ __device__ bool block_merge_runs(const RedState& s, MergeSmem& ms, MergeReq& q, 
     const int r = block_merge_chunked(s, (unsigned char*)&ms, q, p, total);
     if (r >= 0) return r == 1;
   }
-  while (n > 1 || (n == 1 && q.d[0].scale != 1)) {
+  // runs too unevenly spread for one pass: merge them two at a time (two-run
+  // chunked merges always fit; the tile merge takes small pairs)
+  __shared__ RunDesc tree[32];
+  if (threadIdx.x < n) tree[threadIdx.x] = q.d[threadIdx.x];
+  __syncthreads();
+  while (n > 1 || (n == 1 && tree[0].scale != 1)) {
     const uint32_t h = n > 1 ? n >> 1 : 1;
     for (uint32_t i = 0; i < h; ++i) {
-      const RunDesc A = q.d[2 * i];
-      const RunDesc Bd = n > 1 ? q.d[2 * i + 1] : none;
+      const RunDesc A = tree[2 * i];
+      const RunDesc Bd = n > 1 ? tree[2 * i + 1] : none;
       const unsigned long long want = (unsigned long long)A.len + Bd.len;
+      if (n > 1 && want > SMALL_MERGE_USE) {
+        __syncthreads();  // every thread has read tree[2i], tree[2i + 1]
+        if (threadIdx.x == 0) {
+          q.d[0] = A;
+          q.d[1] = Bd;
+          q.n = 2;
+        }
+        __syncthreads();
+        const int r = block_merge_chunked(s, (unsigned char*)&ms, q, p, (uint32_t)want);
+        if (r == 0) return false;
+        if (r == 1) {
+          if (threadIdx.x == 0) tree[i] = q.d[0];
+          __syncthreads();
+          continue;
+        }
+      }
       if (threadIdx.x == 0) block_reserve(s, q, want ? want : 1ull);
       __syncthreads();
       const unsigned long long off = q.off;
       if (off + want > s.r_cap) return false;
       const uint32_t len = block_axpy(ms, A, Bd, p, s.r_key + off, s.r_coef + off);
       if (threadIdx.x == 0) {
-        q.d[i] = RunDesc{s.r_key + off, s.r_coef + off, len, 1};
+        tree[i] = RunDesc{s.r_key + off, s.r_coef + off, len, 1};
         atomicAdd(s.compacted, want);
       }
       __syncthreads();
     }
     if (n > 1 && (n & 1)) {
-      if (threadIdx.x == 0) q.d[h] = q.d[n - 1];
+      if (threadIdx.x == 0) tree[h] = tree[n - 1];
       __syncthreads();
     }
     n = n > 1 ? h + (n & 1) : 1;
   }
+  if (threadIdx.x == 0) q.d[0] = tree[0];
+  __syncthreads();
   return true;
 }
 
