@@ -683,14 +683,14 @@ int run_batch(Workspace& w, const float* dD, const std::vector<int64_t>& ns, int
     // The arena holds every run a reduction writes (generated coboundaries,
     // merges, stored columns), which long chains make large; an arena that
     // proves too small costs a rerun of the dimension with 8x the room, so a
-    // first call starts at up to 2^28 entries (3 GB) when the device has 16x
+    // first call starts at up to 2^30 entries (12 GB) when the device has 16x
     // that free (the workspace keeps it for later calls).
     size_t rcap = lim.arena_entries ? (size_t)lim.arena_entries
                                     : std::max<size_t>(w.r_cap, std::max<size_t>(16 * (size_t)M, (size_t)1 << 22));
     if (!lim.arena_entries && M > 4096) {
       size_t free_b = 0, total_b = 0;
       if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
-        const size_t roomy = std::min<size_t>((size_t)1 << 28, free_b / 16 / 12);
+        const size_t roomy = std::min<size_t>((size_t)1 << 30, free_b / 16 / 12);
         rcap = std::max(rcap, roomy);
       } else {
         cudaGetLastError();

@@ -1232,15 +1232,18 @@ __device__ int chain_advance(const DimArgs& a, const RedState& s, const CV& cv, 
       wcoef = tcoef;
     } else {
       const uint32_t k = (uint32_t)ch.owner;
+      // the owner's coefficient, stored run and simplex, read at once
       wcoef = s.piv_coef[k];
-      if (s.r_len[k]) {
-        wk = s.r_key + s.r_off[k];
-        wc = s.r_coef + s.r_off[k];
-        wn = s.r_len[k];
+      const uint32_t kn = s.r_len[k];
+      const unsigned long long ko = s.r_off[k];
+      const uint64_t kkey = s.col_keys[k];
+      if (kn) {
+        wk = s.r_key + ko;
+        wc = s.r_coef + ko;
+        wn = kn;
       } else {
-        uint64_t kidx;
-        uint32_t kr, kcl;
-        column_simplex(a, s, k, &kidx, &kr, &kcl);
+        const uint64_t kidx = kkey & low_mask(a.col_bits);
+        const uint32_t kr = a.rank_max - (uint32_t)((kkey >> a.col_bits) & low_mask(a.rank_bits));
         if (!gen_sorted(a, s, cv, B, lane, tile, kidx, false, kr, &wk, &wc, &wn)) return CH_ARENA;
       }
     }
@@ -2709,16 +2712,13 @@ __device__ __forceinline__ uint64_t ring_pivot(const Rings& R, RingRun& rs, int 
       *coef_out = cs;
       return m;
     }
-    if (Z2) {
-      r.cur = at ? c1 : r.cur;
-      r.hk = hk2;
-      r.nk = nk2;
-    } else if (at) {
-      r.cur = c1;
-      r.hk = hk2;
-      r.nk = nk2;
-      r.hc = r.nc;
-      r.nc = more ? mod(R.c[x] * r.scale) : 0u;
+    r.cur = at ? c1 : r.cur;  // no divergent branch: every lane selects
+    r.hk = hk2;
+    r.nk = nk2;
+    if (!Z2) {
+      const uint32_t nc2 = more ? mod(R.c[x] * r.scale) : 0u;
+      r.hc = at ? r.nc : r.hc;
+      r.nc = at ? nc2 : r.nc;
     }
     if (sum >> (Z2 ? 16 : 24)) {  // refill the rings that ran dry (the head stays; the entry after it is reloaded)
       unsigned need = __ballot_sync(0xffffffffu, refill);
@@ -2850,19 +2850,20 @@ __device__ int chainb_advance(const DimArgs& a, const RedState& s, const CV& cv,
       return CH_GEN;
     }
     const uint32_t k = (uint32_t)ch.owner;
+    // the owner's coefficient, stored run and simplex, read at once
     const uint32_t wcoef = s.piv_coef[k];
     const uint32_t kn = s.r_len[k];
+    const unsigned long long ko = s.r_off[k];
+    const uint64_t kkey = s.col_keys[k];
     if (!kn) {
-      uint64_t kidx;
-      uint32_t kr, kcl;
-      column_simplex(a, s, k, &kidx, &kr, &kcl);
+      const uint64_t kidx = kkey & low_mask(a.col_bits);
+      const uint32_t kr = a.rank_max - (uint32_t)((kkey >> a.col_bits) & low_mask(a.rank_bits));
       req->gidx = kidx;
       req->grank = kr;
       req->gpacked = false;
       ch.pcoef = wcoef;
       return CH_GEN;
     }
-    const unsigned long long ko = s.r_off[k];
     chainb_add(a, s, R, ch, lane, s.r_key + ko, s.r_coef + ko, kn, wcoef);
   }
 }
