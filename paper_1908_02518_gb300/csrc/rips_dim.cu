@@ -2497,7 +2497,10 @@ __device__ int block_merge_chunked(const RedState& s, unsigned char* raw, MergeR
   }
   uint64_t* fk = s.r_key + off;
   uint32_t* fc = s.r_coef + off;
-  if (s.help && K >= HELP_MIN_CHUNKS && *(volatile const unsigned*)s.idle >= HELP_MIN_IDLE) {
+  __shared__ int share;  // read by thread 0 for the whole block: the count changes under other blocks
+  if (tid == 0) share = s.help && K >= HELP_MIN_CHUNKS && *(volatile const unsigned*)s.idle >= HELP_MIN_IDLE;
+  __syncthreads();
+  if (share) {
     const int r = block_merge_helped(s, raw, q, p, total, K, bnd, fk, fc);
     if (r != -2) return r;  // else the board is taken: merge here
   }
@@ -3117,7 +3120,12 @@ __global__ void __launch_bounds__(256, 2) reduce_persistent_kernel(DimArgs a, Re
     const int src = r & 1, dst = src ^ 1;
     const uint32_t nclaim = *(volatile unsigned*)&claim_cnt[src];
     const uint32_t nqueued = *(volatile unsigned*)&heavy_cnt[src];
-    const uint32_t errs = *(volatile uint32_t*)a.err;
+    // the error word changes under other blocks: thread 0 reads it for the
+    // whole block, so its threads leave the loop together
+    __shared__ uint32_t errs_seen;
+    if (threadIdx.x == 0) errs_seen = *(volatile uint32_t*)a.err;
+    __syncthreads();
+    const uint32_t errs = errs_seen;
     if ((nclaim == 0 && nqueued == 0) || (errs & (ERRF_ARENA | ERRF_TIMEOUT | ERRF_INTERNAL | ERRF_TABLE_FULL)))
       break;
     for (uint32_t t = tid; t < nclaim; t += threads)
