@@ -249,10 +249,11 @@ __device__ __forceinline__ bool cofacet_of(const CV& cv, const Binom& B, const i
     r = max(r, x);
     c += v[l] > j;
   }
+  const uint64_t bj = B(j, d + 2 - c);  // loaded beside the rank lookups, not after them
   if (!ok) return false;
   *rank = r;
   *cpos = c;
-  *idx = cs.above[c] + B(j, d + 2 - c) + cs.below[c];
+  *idx = cs.above[c] + bj + cs.below[c];
   return true;
 }
 
@@ -2641,8 +2642,8 @@ __device__ __forceinline__ void ring_load(const Rings& R, RingRun& r, int lane, 
   const uint32_t i = base + lane;
   if (i < len) {
     const uint32_t at = slot * RING_W + (i & (RING_W - 1));
-    R.k[at] = sk ? sk[i] : kp[i];
-    R.c[at] = p == 2 ? 1u : (sc ? sc[i] : cp[i]);
+    R.k[at] = sk ? sk[i] : __ldcg(kp + i);  // through L2: runs may come from other blocks
+    R.c[at] = p == 2 ? 1u : (sc ? sc[i] : __ldcg(cp + i));
   }
   __syncwarp();
   if (lane == L) {
