@@ -71,6 +71,8 @@ def _load():
     lib.oracle_result_stats.restype = C.c_int
     lib.oracle_result_free.argtypes = [C.c_void_p]
     lib.oracle_result_free.restype = None
+    lib.oracle_result_cocycle.argtypes = [C.c_void_p, C.c_int64, i64p, C.POINTER(C.c_uint32), C.c_int64]
+    lib.oracle_result_cocycle.restype = C.c_int64
     lib.oracle_simplex_index.argtypes = [i64p, C.c_int32]
     lib.oracle_simplex_index.restype = C.c_int64
     lib.oracle_simplex_vertices.argtypes = [C.c_int64, C.c_int32, C.c_int64, i64p]
@@ -116,6 +118,9 @@ class OracleResult:
     bars: np.ndarray          # fields dim, birth, death, birth_simplex, death_simplex
     threshold: float          # effective threshold used
     stats: list               # list of dicts per dimension 0..dim_max
+    # with cocycles=True: per bar (same order), its representative cocycle as
+    # (d-simplex indices, Z/p coefficients), empty for H0 bars
+    cocycles: list | None = None
 
     def dim(self, d: int) -> np.ndarray:
         return self.bars[self.bars["dim"] == d]
@@ -126,12 +131,14 @@ BAR_DTYPE = np.dtype([("dim", np.int32), ("birth", np.float32), ("death", np.flo
 
 
 def barcodes(dist, dim_max: int, threshold: float = math.inf, p: int = 2,
-             method: str = "coh", keep_zero: bool = False) -> OracleResult:
+             method: str = "coh", keep_zero: bool = False, cocycles: bool = False) -> OracleResult:
     """Persistence barcodes H0..H_dim_max of the Rips filtration of ``dist``.
 
     With ``keep_zero`` the zero-persistence pairs are listed as bars too (birth
     equal to death), which exposes every persistence pair of the refined
-    filtration.
+    filtration.  With ``cocycles`` (method "coh") every bar of dimension d >= 1
+    also gets its representative cocycle: the column V_j of the coboundary
+    reduction of its birth simplex (Sections 3.1 and 3.4), R_j = delta V_j.
     """
     lib = _load()
     d = _as_matrix(dist)
@@ -161,10 +168,20 @@ def barcodes(dist, dim_max: int, threshold: float = math.inf, p: int = 2,
             lib.oracle_result_stats(out, k, C.byref(s))
             stats.append({f: int(getattr(s, f)) for f, _ in _Stats._fields_})
         t = float(lib.oracle_result_threshold(out))
+        cocs = None
+        if cocycles:
+            cocs = []
+            for q in range(nb):
+                ln = int(lib.oracle_result_cocycle(out, q, None, None, 0))
+                idx = np.zeros(max(ln, 1), dtype=np.int64)
+                cf = np.zeros(max(ln, 1), dtype=np.uint32)
+                if ln > 0:
+                    lib.oracle_result_cocycle(out, q, _i64(idx), cf.ctypes.data_as(C.POINTER(C.c_uint32)), ln)
+                cocs.append((idx[:ln], cf[:ln]))
     finally:
         lib.oracle_result_free(out)
     order = np.lexsort((arr["birth_simplex"], arr["death"], arr["birth"], arr["dim"]))
-    return OracleResult(arr[order], t, stats)
+    return OracleResult(arr[order], t, stats, [cocs[i] for i in order] if cocs is not None else None)
 
 
 def simplex_index(vertices) -> int:

@@ -223,8 +223,15 @@ static int vertex_list(int64_t n, vec* out) {
 /* ------------------------------------------------------------------------- */
 /* result object                                                             */
 
+/* where a bar's representative cocycle lies in the result's entry pool */
+typedef struct {
+  int64_t off, len;
+} cospan;
+
 struct oracle_result {
   vec bars;
+  vec cospans; /* one per bar (len 0: none recorded) */
+  vec copool;  /* oracle_cocycle_entry */
   float t;
   int32_t dim_max;
   int32_t keep_zero; /* also list zero-persistence pairs as bars */
@@ -233,7 +240,9 @@ struct oracle_result {
 
 static int add_bar(oracle_result* r, int32_t dim, float b, float dth, int64_t bs, int64_t ds) {
   oracle_bar x = {dim, b, dth, bs, ds};
-  return vec_push(&r->bars, &x);
+  cospan none = {0, 0};
+  if (vec_push(&r->bars, &x)) return -3;
+  return vec_push(&r->cospans, &none);
 }
 
 int64_t oracle_result_num_bars(const oracle_result* r) { return r ? r->bars.n : -1; }
@@ -247,7 +256,21 @@ int oracle_result_stats(const oracle_result* r, int32_t dim, oracle_dim_stats* o
 void oracle_result_free(oracle_result* r) {
   if (!r) return;
   vec_free(&r->bars);
+  vec_free(&r->cospans);
+  vec_free(&r->copool);
   free(r);
+}
+
+int64_t oracle_result_cocycle(const oracle_result* r, int64_t bar, int64_t* idx_out, uint32_t* coef_out,
+                              int64_t cap) {
+  if (!r || bar < 0 || bar >= r->cospans.n || cap < 0 || (cap > 0 && (!idx_out || !coef_out))) return -1;
+  const cospan sp = ((const cospan*)r->cospans.p)[bar];
+  const oracle_cocycle_entry* e = (const oracle_cocycle_entry*)r->copool.p + sp.off;
+  for (int64_t q = 0; q < sp.len && q < cap; q++) {
+    idx_out[q] = e[q].idx;
+    coef_out[q] = e[q].c;
+  }
+  return sp.len;
 }
 
 int64_t oracle_simplex_index(const int64_t* verts, int32_t d) {
@@ -871,6 +894,23 @@ static int vadd(vec* V, const vent* w, int64_t wl, uint32_t lam, uint32_t p) {
   return 0;
 }
 
+/* The representative cocycle of the bar just added: the column V_j of the
+ * reduction, R_j = delta V_j (Sections 3.1 and 3.4), as (simplex index,
+ * coefficient) in increasing index order.  For an essential class R_j = 0, so
+ * V_j is a cocycle; for a pair (sigma_j, tau) delta V_j vanishes on every
+ * (d+1)-simplex older than tau and not on tau. */
+static int record_cocycle(oracle_result* res, const vec* V) {
+  cospan* sp = (cospan*)res->cospans.p + (res->cospans.n - 1);
+  sp->off = res->copool.n;
+  sp->len = V->n;
+  for (int64_t q = 0; q < V->n; q++) {
+    const vent* v = &AT(*V, vent, q);
+    oracle_cocycle_entry e = {v->idx, v->c};
+    if (vec_push(&res->copool, &e)) return -3;
+  }
+  return 0;
+}
+
 static int oracle_coh(const float* D, int64_t n, int32_t dim_max, float t, uint32_t p,
                       oracle_result* res) {
   binom_t b;
@@ -1012,12 +1052,16 @@ static int oracle_coh(const float* D, int64_t n, int32_t dim_max, float t, uint3
       if (pi < 0) {
         res->stats[d].essential++;
         rc = add_bar(res, d, sj.diam, INFINITY, sj.idx, -1);
+        if (!rc) rc = record_cocycle(res, &V);
       } else {
         rc = hmap_put(&piv, pv.idx, j);
         pivc[j] = pv.c;
         res->stats[d].pairs++;
         if (pv.diam == sj.diam) res->stats[d].zero_pairs++;
-        if (!rc && (pv.diam != sj.diam || res->keep_zero)) rc = add_bar(res, d, sj.diam, pv.diam, sj.idx, pv.idx);
+        if (!rc && (pv.diam != sj.diam || res->keep_zero)) {
+          rc = add_bar(res, d, sj.diam, pv.diam, sj.idx, pv.idx);
+          if (!rc) rc = record_cocycle(res, &V);
+        }
         simp cl = {pv.idx, pv.diam};
         if (!rc) rc = vec_push(&next_cleared, &cl);
         /* store V_j for this death column (only if it is not just e_j) */
@@ -1064,6 +1108,8 @@ int oracle_barcodes(const float* D, int64_t n, int32_t dim_max, float threshold,
   oracle_result* r = (oracle_result*)calloc(1, sizeof(oracle_result));
   if (!r) return -3;
   r->bars.elem = sizeof(oracle_bar);
+  r->cospans.elem = sizeof(cospan);
+  r->copool.elem = sizeof(oracle_cocycle_entry);
   r->t = t;
   r->dim_max = dim_max;
   r->keep_zero = keep_zero;

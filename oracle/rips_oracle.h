@@ -63,6 +63,21 @@ float oracle_result_threshold(const oracle_result* r);
 int oracle_result_stats(const oracle_result* r, int32_t dim, oracle_dim_stats* out);
 void oracle_result_free(oracle_result* r);
 
+/* Representative cocycles (ORACLE_COH only; Sections 3.1 and 3.4): for a bar of
+ * dimension d >= 1, the column V_j of the coboundary reduction whose column j
+ * is the bar's birth simplex, so that R_j = delta V_j.  An essential bar's
+ * cocycle has a zero coboundary; a finite bar's coboundary vanishes on every
+ * (d+1)-simplex older than its death simplex and not on the death simplex.
+ * Entries are (d-simplex index, coefficient in Z/p), increasing index. */
+typedef struct {
+  int64_t idx;
+  uint32_t c;
+} oracle_cocycle_entry;
+/* Copies up to cap entries of bar `bar`'s cocycle; returns its length (0 for
+ * H0 bars and for the ORACLE_DEF method), -1 on bad arguments. */
+int64_t oracle_result_cocycle(const oracle_result* r, int64_t bar, int64_t* idx_out, uint32_t* coef_out,
+                              int64_t cap);
+
 /* Combinatorial number system (Section 2): index of the simplex with vertices
  * verts[0..d] (any order, distinct). */
 int64_t oracle_simplex_index(const int64_t* verts, int32_t d);
